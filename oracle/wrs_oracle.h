@@ -1,0 +1,108 @@
+/*
+ * CPU oracle for per-pixel weighted reservoir sampling on foveated frame
+ * streams ("Enhancing Foveated Rendering with Weighted Reservoir Sampling").
+ *
+ * TEST INFRASTRUCTURE ONLY. Plain, slow, obviously correct C. Only the test
+ * suite, the smoke check and the CPU-baseline leg of the benchmark may load
+ * it; the product path never does. It shares no source, header, table or
+ * constant with the CUDA library: both follow the same written operation
+ * sequence independently.
+ *
+ * Parity status of each function is given beside it; "pinned" names what
+ * outside fact checks it in tests/test_oracle_pins.py.
+ */
+#ifndef WRS_ORACLE_H
+#define WRS_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_EMPTY 0xFFFFFFFFu
+
+typedef struct {
+  int32_t width, height;   /* frame size in pixels */
+  int32_t K;               /* reservoir slots per pixel, 1..16 */
+  float r_f;               /* foveal radius in pixels */
+  float deg_per_px;        /* eccentricity per pixel in degrees; <= 0 selects 2.5 / r_f */
+  uint64_t seed;           /* Philox key */
+  uint32_t stream_id;      /* third Philox counter word */
+  int32_t temporal_bias;   /* 1: apply Eq. (temporal-bias) before combining */
+} orc_config;
+
+/* FP32 exp for x in [-87, 0]: range reduction by ln 2 and a degree-7 Taylor
+ * polynomial. Pinned: libm exp within 4 ulp (closed form). */
+float orc_exp(float x);
+/* FP32 natural log for u in (0, 1): mantissa/exponent split and the atanh
+ * series. Pinned: libm log within 4 ulp. */
+float orc_log(float u);
+/* Philox4x32-10 (Salmon et al., SC'11). Pinned: curand's Philox4_32_10
+ * (GPU test) and uniformity statistics. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* The uniform draw of pixel p at frame t, in (0, 1). */
+float orc_uniform(uint64_t seed, uint32_t stream_id, uint32_t t, int64_t p);
+/* Eq. (cone_retinal_density), plain FP64 with libm exp. Pinned: d(0), the
+ * derivative at 0 and the large-e asymptote (closed forms). */
+double orc_density64(double e);
+/* The same density without the cancelling factor 2 d_c(0), in the fixed FP32
+ * sequence the bit-exact path uses. Pinned: orc_density64 within 1e-6. */
+float orc_density32(float e);
+/* Eq. (phat) for the pixel (x, y) and gaze (gx, gy), fixed FP32 sequence.
+ * Pinned: w = 1 inside the fovea, continuity at r_f, monotone decrease,
+ * 0 < w <= 1, FP64 value within 1e-6. */
+float orc_weight32(const orc_config* cfg, int32_t x, int32_t y, float gx, float gy);
+float orc_delta(const orc_config* cfg);
+
+/* One candidate entering one pixel's reservoir: Eq. (temporal-bias) on the
+ * history, then Alg. 2 in its exponential-key form (keep the K smallest keys
+ * E/w scaled by the running bias product P). Pinned statistically:
+ * Eq. (chao-selection-probability) for K = 1, successive sampling without
+ * replacement for K > 1 (brute force), uniform subsets for equal weights,
+ * literal Alg. 2 equivalence, size <= K. */
+void orc_pixel_step(int K, int bias, float w, float u, uint32_t t, const float rgb_in[3],
+                    int flush, float* W, float* P, float* key, uint32_t* idx, float* wt,
+                    float* rgb);
+/* Weighted combination of the occupied slots, FP64. Pinned: K = 1 returns the
+ * resident sample, equal colours return that colour, no slot returns 0. */
+void orc_resolve_pixel(int K, const uint32_t* idx, const float* wt, const float* rgb,
+                       double out[3]);
+
+/* Pixel-major state of n pixels: W[n], P[n], key[n][K], idx[n][K], wt[n][K],
+ * rgb[n][K][3]. */
+void orc_init_state(int K, int64_t n, float* W, float* P, float* key, uint32_t* idx,
+                    float* wt, float* rgb);
+/* One frame. frame is [height][pitch] floats holding RGB triples; fov_map is
+ * [height][width] bytes or NULL (0xFF flushes the pixel). pix lists the
+ * pixels to simulate (state index i belongs to pixel pix[i]); NULL means all
+ * pixels in row-major order. Returns 0, or -1 on bad arguments. */
+int orc_push_frame(const orc_config* cfg, uint32_t t, const float* frame, int64_t pitch,
+                   float gx, float gy, const uint8_t* fov_map, int64_t npix,
+                   const int64_t* pix, float* W, float* P, float* key, uint32_t* idx,
+                   float* wt, float* rgb, int nthreads);
+void orc_resolve(int K, int64_t npix, const uint32_t* idx, const float* wt, const float* rgb,
+                 double* out, int nthreads);
+
+/* Statistics harness: n_trials independent single-pixel streams of n_items
+ * candidates with weights w[n_items] and uniforms u[n_trials][n_items].
+ * Writes the final slot frame indices [n_trials][K] and final W. */
+void orc_run_streams(int K, int bias, int64_t n_trials, int n_items, const float* w,
+                     const float* u, uint32_t* final_idx, float* final_W);
+/* Literal n = 1 form: Eq. (temporal-bias) then Alg. 2 with rand * (R1 + R2) <= R1. */
+void orc_chao_literal(int bias, int64_t n_trials, int n_items, const float* w,
+                      const float* u, uint32_t* final_idx);
+
+/* Element-wise helpers for tests. */
+void orc_exp_n(const float* x, float* y, int64_t n);
+void orc_log_n(const float* x, float* y, int64_t n);
+void orc_density32_n(const float* e, float* y, int64_t n);
+void orc_density64_n(const double* e, double* y, int64_t n);
+void orc_uniform_n(uint64_t seed, uint32_t stream_id, uint32_t t, int64_t p0, int64_t n,
+                   float* u);
+void orc_weight32_grid(const orc_config* cfg, float gx, float gy, float* w);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,71 @@
+"""The seeded input generators: determinism, ranges and ring structure."""
+import numpy as np
+import torch
+
+from synth import Foveator, box_pyramid, gaze_path, ground_truth, workload
+
+
+def test_ground_truth_deterministic_and_in_range():
+    a = ground_truth(97, 53, seed=3)
+    b = ground_truth(97, 53, seed=3)
+    c = ground_truth(97, 53, seed=4)
+    assert a.shape == (53, 97, 3) and a.dtype == np.float32
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    assert a.min() >= 0.0 and a.max() <= 1.0
+
+
+def test_box_pyramid_block_means():
+    img = ground_truth(37, 21, seed=1)
+    pyr = box_pyramid(img, 4)
+    assert np.array_equal(pyr[0], img)
+    for lev in (1, 2, 3):
+        b = 1 << lev
+        for (y, x) in ((0, 0), (20, 36), (9, 17)):
+            by, bx = (y // b) * b, (x // b) * b
+            blk = img[by:by + b, bx:bx + b].astype(np.float64).mean(axis=(0, 1))
+            assert np.allclose(pyr[lev, y, x], blk, rtol=0, atol=1e-6)
+
+
+def test_foveated_frame_rings():
+    fv = Foveator(64, 48, (8.0, 20.0), seed=2)
+    fr, lev = fv.frame(30.25, 20.5)
+    yy, xx = np.mgrid[0:48, 0:64]
+    d2 = ((xx + 0.5) - 30.25) ** 2 + ((yy + 0.5) - 20.5) ** 2
+    expect = (d2 > 64.0).astype(np.uint8) + (d2 > 400.0).astype(np.uint8)
+    assert np.array_equal(lev.numpy(), expect)
+    pyr = box_pyramid(fv.ground_truth.numpy(), 3)
+    ref = np.take_along_axis(pyr.reshape(3, -1, 3), expect.reshape(1, -1, 1).astype(np.int64), 0)
+    assert np.array_equal(fr.numpy().reshape(-1, 3), ref[0])
+
+
+def test_foveator_float64_path_is_exact_across_devices():
+    # the ring test uses float64 sub/mul/add only; check it against exact rationals
+    fv = Foveator(16, 16, (3.0,), seed=0)
+    lev = fv.ring_map(7.75, 8.5).numpy()
+    for y in range(16):
+        for x in range(16):
+            dx, dy = x + 0.5 - 7.75, y + 0.5 - 8.5
+            assert lev[y, x] == (dx * dx + dy * dy > 9.0)
+    assert torch.equal(fv.ring_map(7.75, 8.5), fv.ring_map(7.75, 8.5))
+
+
+def test_gaze_paths():
+    g = gaze_path(1920, 1080, 120, seed=0)
+    assert g.shape == (120, 2) and g.dtype == np.float32
+    assert np.all((g[:, 0] >= 0) & (g[:, 0] <= 1920) & (g[:, 1] >= 0) & (g[:, 1] <= 1080))
+    assert np.array_equal(g, gaze_path(1920, 1080, 120, seed=0))
+    # within a fixation the spread is the jitter; across saccades it is large
+    fix = g[1:27]
+    assert np.std(fix[:, 0]) < 15 and np.std(fix[:, 1]) < 15
+    j = gaze_path(256, 256, 5000, seed=0, model="jitter", jitter_px=4.0)
+    assert abs(np.std(j[:, 0]) - 4.0) < 0.3 and abs(np.mean(j[:, 1]) - 128.0) < 0.3
+
+
+def test_workloads():
+    assert workload("tiny").pixels == 65536
+    assert workload("hd").pixels == 2073600
+    assert workload("4k").pixels == 8294400
+    mix = workload("mix16")
+    assert len(mix.streams) == 16 and mix.pixels == 68917248
+    assert [s.K for s in mix.streams[:4]] == [8, 4, 8, 4]
+    assert all(s.color_fp16 for s in mix.streams)
