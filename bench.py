@@ -1,0 +1,395 @@
+"""Benchmark: fused reservoir update + resolve of a 4K foveated stream.
+
+Workload: 3840x2160 RGB, K = 8 slots, FP32 colour planes (``--workload 4k``;
+``4k_fp16`` for FP16 colour planes), fovea 200 px with 2x/4x/8x rings, gaze
+from fixations + saccades, 240 distinct synthetic frames resident in HBM and
+pushed cyclically. One step = one frame pushed through the whole per-pixel
+path (weight, key, temporal bias, K-slot combine, resolve) = one kernel
+launch. The state (1.9 GB per frame touched) is far larger than the 129 MB
+L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle
+instead (the method has no reference GPU implementation).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import Foveator, frame_pixels, gaze_path, workload  # noqa: E402
+
+METRIC = "4K reservoir update+resolve ms/frame, % HBM peak; served p99 latency vs plain"
+UNIT = "ms/frame"
+
+
+def algorithmic_bytes_per_px(K: int, fp16: bool) -> int:
+    """Bytes one pixel-update must move: frame RGB in (12), resolved RGB out
+    (12), W and P read and written (16), every slot's key, weight and colour
+    read (K * (8 + 3c)); replacement writes excluded (they depend on the
+    stream)."""
+    c = 2 if fp16 else 4
+    return 40 + K * (8 + 3 * c)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 50):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", str(period_ms)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ peaks
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def recorded_traffic(kernel: str, workload_name: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (matched by hash)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        from paper_2510_03964_gb300 import kernel_source_hash
+        ent = d.get(workload_name)
+        if ent and ent.get("kernel") == kernel and ent.get("source_hash") == kernel_source_hash():
+            return ent.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+    return None
+
+
+# ------------------------------------------------------------------ oracle timing
+
+def oracle_ms_per_frame(spec, pixels: np.ndarray, frames: int, nthreads: int,
+                        fv_dev: Foveator, gaze: np.ndarray, budget_s: float | None = None):
+    """Times the oracle on a fixed sample of pixels (every pixel is an
+    independent stream) and scales the mean per-frame time to a full frame."""
+    import oracle
+    st = oracle.OracleStream(spec.width, spec.height, spec.K, spec.r_f, seed=spec.seed,
+                             stream_id=spec.stream_id, temporal_bias=spec.temporal_bias,
+                             pixels=pixels, nthreads=nthreads)
+    host = np.zeros((spec.height, spec.width, 3), np.float32)
+    flat = host.reshape(-1, 3)
+    pix_t = torch.as_tensor(pixels)
+    times = []
+    t_start = time.perf_counter()
+    for t in range(frames):
+        gx, gy = gaze[t % len(gaze)]
+        flat[pixels] = frame_pixels(fv_dev, float(gx), float(gy), pix_t).cpu().numpy()
+        t0 = time.perf_counter()
+        st.push_frame(host, (gx, gy))
+        st.resolve()
+        times.append(time.perf_counter() - t0)
+        if budget_s is not None and time.perf_counter() - t_start > budget_s and t >= 3:
+            break
+    steady = times[1:] if len(times) > 1 else times
+    per_frame = statistics.mean(steady) * (spec.width * spec.height) / len(pixels)
+    return per_frame * 1e3, len(times)
+
+
+def sample_pixels(spec, n: int) -> np.ndarray:
+    hw = spec.width * spec.height
+    stride = max(1, hw // n)
+    return np.arange(0, hw, stride, dtype=np.int64)[:n]
+
+
+# ------------------------------------------------------------------ main arms
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() and args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float, device) -> float:
+    if world == 1:
+        return value
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, world, rank):
+    spec = workload(args.workload).streams[0]
+    if rank != 0:
+        return
+    nthreads = os.cpu_count() or 1
+    fv = Foveator(spec.width, spec.height, spec.radii, seed=spec.seed, device="cpu")
+    gaze = gaze_path(spec.width, spec.height, spec.frames, seed=spec.seed, model=spec.gaze_model,
+                     jitter_px=spec.jitter_px)
+    pixels = sample_pixels(spec, args.ref_sample)
+    import oracle
+    st = oracle.OracleStream(spec.width, spec.height, spec.K, spec.r_f, seed=spec.seed,
+                             stream_id=spec.stream_id, temporal_bias=spec.temporal_bias,
+                             pixels=pixels, nthreads=nthreads)
+    host = np.zeros((spec.height, spec.width, 3), np.float32)
+    flat = host.reshape(-1, 3)
+    pix_t = torch.as_tensor(pixels)
+    # inputs for the sampled pixels of every distinct frame, made before timing
+    cols = [frame_pixels(fv, float(g[0]), float(g[1]), pix_t).numpy() for g in gaze]
+    times = []
+    for step in range(args.warmup + args.steps):
+        t = step % len(gaze)
+        flat[pixels] = cols[t]
+        t0 = time.perf_counter()
+        st.push_frame(host, gaze[t])
+        st.resolve()
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    scale = spec.width * spec.height / len(pixels)
+    ms = statistics.mean(times) * scale * 1e3
+    sample = (f"{len(pixels)} of {spec.width * spec.height} pixels (every "
+              f"{spec.width * spec.height // len(pixels)}th) per step, scaled to a full frame")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(ms, 4), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config(spec, args.workload),
+        "cpu_baseline": {"value": round(ms, 4), "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(ms, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(spec, name):
+    return {"workload": f"{name}: {spec.width}x{spec.height} RGB, K={spec.K}, "
+                        f"{'FP16' if spec.color_fp16 else 'FP32'} colour planes, fovea {spec.r_f:g} px, "
+                        f"rings {','.join(f'{r:g}' for r in spec.radii)} px, {spec.frames} distinct frames "
+                        f"pushed cyclically, temporal bias {'on' if spec.temporal_bias else 'off'}",
+            "width": spec.width, "height": spec.height, "K": spec.K,
+            "color": "fp16" if spec.color_fp16 else "fp32", "frames_distinct": spec.frames,
+            "l2": "state+frame traffic per step far above the 129 MB L2; no flush",
+            "parallelism": "replicas (one independent stream per GPU)"}
+
+
+def run_ours(args, world, rank, local):
+    import paper_2510_03964_gb300 as wrs
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    spec = workload(args.workload).streams[0]
+    seed = spec.seed + rank
+    fv = Foveator(spec.width, spec.height, spec.radii, seed=seed, device=dev)
+    gaze = gaze_path(spec.width, spec.height, spec.frames, seed=seed, model=spec.gaze_model,
+                     jitter_px=spec.jitter_px)
+    hw = spec.width * spec.height
+    frames = torch.empty((spec.frames, spec.height, spec.width, 3), dtype=torch.float32, device=dev)
+    for t in range(spec.frames):
+        fv.frame(float(gaze[t, 0]), float(gaze[t, 1]), out=frames[t])
+    out = torch.empty((spec.height, spec.width, 3), dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    st = wrs.Stream(spec.width, spec.height, spec.K, spec.r_f, seed=seed, stream_id=spec.stream_id,
+                    color_fp16=spec.color_fp16, temporal_bias=spec.temporal_bias, device=dev,
+                    stream=stream)
+    if args.block or args.px:
+        st.set_launch(args.block, args.px)
+    torch.cuda.synchronize()
+
+    def push(t):
+        st.push_frame(frames[t % spec.frames], gaze[t % spec.frames], None, out, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for t in range(args.warmup):
+            push(t)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local) if rank == 0 else None
+    time.sleep(0.3 if clocks else 0.0)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            starts[i].record(stream)
+            push(args.warmup + i)
+            ends[i].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop() if clocks else None
+    total_ms = starts[0].elapsed_time(ends[-1])
+    kernel_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = max_over_ranks(world, total_ms, dev)
+    ms_frame = total_ms / (args.steps * world)
+    kernel_avg = statistics.mean(kernel_ms)
+
+    # end-to-end through the host-buffer entry point (copies inside the timed region)
+    e2e = None
+    if args.e2e_steps > 0:
+        pool = min(spec.frames, 8)
+        h_frames = torch.empty((pool, spec.height, spec.width, 3), dtype=torch.float32, pin_memory=True)
+        for i in range(pool):
+            h_frames[i].copy_(frames[i])
+        h_out = torch.empty((spec.height, spec.width, 3), dtype=torch.float32, pin_memory=True)
+        d_in = torch.empty_like(frames[0])
+        d_out = torch.empty_like(out)
+        st2 = wrs.Stream(spec.width, spec.height, spec.K, spec.r_f, seed=seed,
+                         stream_id=spec.stream_id, color_fp16=spec.color_fp16,
+                         temporal_bias=spec.temporal_bias, device=dev, stream=stream)
+        torch.cuda.synchronize()
+        for t in range(3):
+            st2.push_frame_host(h_frames[t % pool], gaze[t % pool], h_out, d_in, d_out, stream=stream)
+        barrier(world)
+        t0 = time.perf_counter()
+        for t in range(args.e2e_steps):
+            st2.push_frame_host(h_frames[t % pool], gaze[t % pool], h_out, d_in, d_out, stream=stream)
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3
+        e2e_ms = max_over_ranks(world, e2e_ms, dev)
+        e2e = {"value": round(e2e_ms / (args.e2e_steps * world), 4), "unit": UNIT,
+               "h2d_bytes_per_step": hw * 12, "d2h_bytes_per_step": hw * 12,
+               "steps": args.e2e_steps,
+               "note": f"wrs_push_frame_host: pinned host frame -> device, fused kernel, resolved "
+                       f"frame -> pinned host, synchronised every step; {pool} host frames cycled"}
+        st2.close()
+
+    if rank != 0:
+        st.close()
+        return
+
+    peaks = measured_peaks()
+    bpp = algorithmic_bytes_per_px(spec.K, spec.color_fp16)
+    achieved = bpp * hw / (kernel_avg * 1e-3) / 1e9
+    kname = f"push_kernel<K={spec.K},{'fp16' if spec.color_fp16 else 'fp32'}>"
+    line = {
+        "metric": METRIC, "value": round(ms_frame, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config(spec, args.workload),
+        "mpx_updates_per_s": round(hw * world / (ms_frame * 1e-3) / 1e6, 1),
+        "kernel_ms_avg": round(kernel_avg, 4),
+        "kernel_ms_median": round(statistics.median(kernel_ms), 4),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                     "traffic": recorded_traffic(kname, args.workload),
+                     "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs, copy)",
+                     "algorithmic_bytes_per_px": bpp, "kernel": kname},
+        "pct_nominal_8tbs": round(100 * achieved / 8000.0, 2),
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if args.cpu_baseline:
+        nthreads = os.cpu_count() or 1
+        pixels = sample_pixels(spec, args.cpu_sample)
+        ms_cpu, nfr = oracle_ms_per_frame(spec, pixels, spec.frames, nthreads, fv, gaze,
+                                          budget_s=args.cpu_budget_s)
+        line["cpu_baseline"] = {
+            "value": round(ms_cpu, 3), "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"{len(pixels)} of {hw} pixels (every {hw // len(pixels)}th), {nfr} frames, "
+                      f"mean of frames 1.. scaled to a full frame; oracle threads over pixels"}
+    st.close()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="4k", choices=["4k", "4k_fp16", "hd"])
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--px", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--cpu-sample", type=int, default=131072)
+    ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    ap.add_argument("--ref-sample", type=int, default=65536)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

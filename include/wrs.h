@@ -1,0 +1,165 @@
+/*
+ * libwrs: per-pixel weighted reservoir sampling of foveated frame streams on
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: "Enhancing Foveated Rendering with Weighted Reservoir Sampling"
+ * (arXiv 2510.03964). Every pixel location is an independent stream that
+ * receives one candidate sample per frame (Sec. 4.1). The candidate's weight
+ * is the normalised retinal density at its eccentricity from that frame's
+ * gaze point (Eq. (cone_retinal_density), Eq. (phat)). The history held in
+ * the reservoir is biased by the new candidate's survival odds
+ * (Eq. (p_survive_reservoir), Eq. (temporal-bias)) and then combined with it
+ * (Alg. 2). With K slots the combine keeps the K smallest exponential keys
+ * -ln(u)/w (the A-ES key u^(1/w), Sec. 3.1, in log form), u drawn from
+ * Philox4x32-10; with K = 1 this is Alg. 2 in distribution. The output pixel
+ * is the weight-averaged colour of the occupied slots.
+ *
+ * Conventions shared by every call:
+ *  - Status: every int-returning call returns WRS_OK (0) or a WRS_ERR_* code;
+ *    wrs_last_error() then holds a one-line message for the calling thread.
+ *    A call that fails leaves the reservoir state and the frame counter as
+ *    they were.
+ *  - Streams: calls enqueue work on the given CUDA stream (a cudaStream_t
+ *    passed as void*; NULL is the legacy default stream) and return without
+ *    synchronising, except wrs_export_state / wrs_import_state and
+ *    wrs_push_frame_host, which wait for their copies.
+ *  - Memory: all d_* pointers are device memory owned by the caller and only
+ *    borrowed for the call; h_* pointers are host memory (pinned memory gives
+ *    asynchronous copies). The library owns only the context object.
+ *  - Frame counter: t starts at 0 at wrs_create and advances by one on every
+ *    successful push.
+ *  - Images are row-major; colours are RGB float triples.
+ */
+#ifndef WRS_H
+#define WRS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WRS_OK 0
+#define WRS_ERR_ARG 1      /* invalid argument (null, size, alignment, range) */
+#define WRS_ERR_CUDA 2     /* a CUDA call failed (message holds its error string) */
+#define WRS_ERR_BUDGET 3   /* state buffer smaller than wrs_state_bytes() */
+#define WRS_ERR_TIMEOUT 4  /* a bounded device-side wait gave up */
+#define WRS_ERR_STATE 5    /* context in the wrong state (e.g. counter exhausted) */
+
+#define WRS_MAX_K 16
+#define WRS_EMPTY_SLOT 0xFFFFFFFFu /* sample index of an unoccupied slot */
+
+typedef struct wrs_ctx wrs_ctx;
+typedef void* wrs_stream_t; /* cudaStream_t */
+
+/* One frame stream. */
+typedef struct {
+  int32_t width, height;   /* pixels, >= 1; width * height < 2^31 - 64 */
+  int32_t K;               /* reservoir slots per pixel, 1..16 (the paper uses n = 1) */
+  float fovea_radius_px;   /* r_f in pixels (> 0): weight 1 at or inside it (Eq. (phat)) */
+  float deg_per_px;        /* eccentricity scale in degrees per pixel; <= 0 selects
+                              2.5 / fovea_radius_px, so r_f sits at the 2.5 deg where the
+                              paper normalises the weight (Fig. (phat_figure) caption) */
+  uint64_t seed;           /* Philox key */
+  uint32_t stream_id;      /* third Philox counter word; distinct per stream in a batch */
+  int32_t color_fp16;      /* 0: FP32 slot colours; 1: FP16 slot colours (keys, weights and
+                              accumulation stay FP32) */
+  int32_t temporal_bias;   /* 1: apply Eq. (temporal-bias) before each combine (paper);
+                              0: plain weighted sampling */
+} wrs_config;
+
+/* Placement of the state planes inside the caller's state buffer. Every plane
+ * holds `plane_px` entries (width*height rounded up to 64), pixel p at entry p.
+ * Offsets are in bytes from the start of the buffer:
+ *   W        float   running weight sum R.wsum (Alg. 2), biased (Eq. (temporal-bias))
+ *   P        float   product of bias factors since the last rescale
+ *   key[j]   float   stored key of slot j (+inf when empty), at key_off + j*plane_bytes4
+ *   idx[j]   uint32  frame index of the slot's sample (WRS_EMPTY_SLOT when empty)
+ *   wt[j]    float   perceptual weight w of the slot's sample (0 when empty)
+ *   col[c][j] float or half  colour channel c of slot j, at
+ *                    col_off + (c*K + j) * plane_bytes_col (0 when empty) */
+typedef struct {
+  int64_t plane_px;
+  int64_t plane_bytes4;     /* plane_px * 4 */
+  int64_t plane_bytes_col;  /* plane_px * 4 (FP32 colour) or * 2 (FP16 colour) */
+  int64_t W_off, P_off, key_off, idx_off, wt_off, col_off;
+  int64_t total_bytes;
+} wrs_layout;
+
+/* Bytes of device memory one stream's reservoir state needs (its planes are
+ * described by wrs_state_layout), or 0 if cfg is invalid. Host only; no CUDA
+ * call. */
+size_t wrs_state_bytes(const wrs_config* cfg);
+int wrs_state_layout(const wrs_config* cfg, wrs_layout* out);
+
+/* Creates a stream context over d_state (device, >= wrs_state_bytes(cfg),
+ * 256-byte aligned; caller-owned and never freed by the library) and enqueues
+ * its initialisation on `stream`: every slot empty, W = 0, P = 1, t = 0.
+ * Errors: WRS_ERR_ARG (cfg, pointers, alignment), WRS_ERR_BUDGET (too small),
+ * WRS_ERR_CUDA (launch). */
+int wrs_create(const wrs_config* cfg, void* d_state, size_t state_bytes, wrs_stream_t stream,
+               wrs_ctx** out);
+
+/* Pushes frame t into every pixel's reservoir and, if d_out is not NULL,
+ * resolves it in the same pass (one kernel). Per pixel (Sec. 4, in order):
+ * weight w from the eccentricity of the pixel centre to (gaze_x, gaze_y)
+ * (Eq. (cone_retinal_density), Eq. (phat)); key -ln(u)/w from Philox
+ * (A-ES, Sec. 3.1); Eq. (temporal-bias) on the history; Alg. 2 as the key
+ * race over the K slots; then out = sum_j wt_j col_j / sum_j wt_j.
+ *   d_frame     device float [height][frame_pitch_elems], RGB triples in the first
+ *               3*width floats of each row; 4-byte aligned.
+ *   frame_pitch_elems  floats per frame row, >= 3*width.
+ *   gaze_x/y    gaze in pixel coordinates (pixel (x, y) has centre (x+0.5, y+0.5));
+ *               must be finite, may lie outside the image.
+ *   d_fov_map   NULL, or device uint8 [height][width]: 0xFF drops that pixel's
+ *               history before the push (occlusion flush, Sec. 4.3); other
+ *               values are ignored.
+ *   d_out       NULL, or device float [height][width][3]: the resolved frame.
+ * Errors: WRS_ERR_ARG, WRS_ERR_STATE (t would overflow), WRS_ERR_CUDA. */
+int wrs_push_frame(wrs_ctx* ctx, const float* d_frame, int64_t frame_pitch_elems, float gaze_x,
+                   float gaze_y, const uint8_t* d_fov_map, float* d_out, wrs_stream_t stream);
+
+/* Resolves the current reservoirs into d_out (device float [height][width][3])
+ * without pushing: bit-identical to the fused resolve of the last push. Pixels
+ * with no occupied slot resolve to 0. */
+int wrs_resolve(wrs_ctx* ctx, float* d_out, wrs_stream_t stream);
+
+/* Frees the context object (not d_state). NULL is accepted. */
+int wrs_destroy(wrs_ctx* ctx);
+
+/* ------------------------------------------------------------------ extras */
+
+/* Same as wrs_push_frame with host buffers: copies h_frame (float
+ * [height][width][3], contiguous) and h_fov_map (optional) into the caller's
+ * device staging buffers d_frame_stage / d_fov_stage, pushes with fused
+ * resolve into d_out_stage, copies the result to h_out, and waits for the
+ * copies on `stream`. */
+int wrs_push_frame_host(wrs_ctx* ctx, const float* h_frame, float gaze_x, float gaze_y,
+                        const uint8_t* h_fov_map, float* h_out, float* d_frame_stage,
+                        uint8_t* d_fov_stage, float* d_out_stage, wrs_stream_t stream);
+
+/* Copies the whole state buffer to / from host memory (layout per
+ * wrs_state_layout) and waits for the copy. Used for checkpoints, migration
+ * of a stream between devices, and tests. Import also sets the frame counter. */
+int wrs_export_state(wrs_ctx* ctx, void* h_dst, size_t bytes, wrs_stream_t stream);
+int wrs_import_state(wrs_ctx* ctx, const void* h_src, size_t bytes, uint32_t frame_index,
+                     wrs_stream_t stream);
+
+/* Frame counter: frames pushed since create (or the imported index). */
+uint32_t wrs_frame_index(const wrs_ctx* ctx);
+
+/* Launch shape of the fused kernel: threads per block (64..1024, multiple of
+ * 32) and pixels per thread (1, 2 or 4). 0 restores the default. Pixels per
+ * thread above 1 need width divisible by it for vector frame I/O; otherwise
+ * the kernel falls back to per-pixel frame access. */
+int wrs_set_launch(wrs_ctx* ctx, int block_threads, int px_per_thread);
+int wrs_get_launch(const wrs_ctx* ctx, int* block_threads, int* px_per_thread);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* wrs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WRS_H */

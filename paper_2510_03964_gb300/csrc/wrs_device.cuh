@@ -1,0 +1,499 @@
+// Device-side arithmetic of the per-pixel weighted reservoir update (sm_103a).
+//
+// "Enhancing Foveated Rendering with Weighted Reservoir Sampling"
+// (arXiv 2510.03964): weight Eq. (cone_retinal_density) + Eq. (phat) (Sec. 4.1),
+// A-ES keys (Sec. 3.1), Eq. (temporal-bias) (Sec. 4.2), Alg. 2 (Sec. 3.2).
+//
+// Every floating-point step that decides which sample a slot holds is an
+// explicit round-to-nearest intrinsic (__fadd_rn, __fmul_rn, __fdiv_rn,
+// __fsqrt_rn), so the compiler cannot contract or reorder it: the stored keys,
+// indices, weights, W and P are a fixed function of the inputs, bit for bit.
+// The resolve accumulates with explicit fused multiply-adds in slot order, so
+// the fused and standalone resolves agree bit for bit too.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace wrs {
+
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr float kInf = __builtin_huge_valf();
+constexpr float kFltMax = 3.40282346638528859812e+38f;
+
+// ---------------------------------------------------------------- constants
+// ln 2 = LN2_HI + LN2_LO with LN2_HI the 12-significant-bit rounding of ln 2
+// (n * LN2_HI exact for |n| < 4096) and LN2_LO the float nearest the rest.
+constexpr float kLn2Hi = 0x1.62ep-1f;
+constexpr float kLn2Lo = 0x1.0bfbe8p-15f;
+constexpr float kLog2e = 0x1.715476p+0f;   // float nearest 1/ln 2
+constexpr float kSqrt2 = 0x1.6a09e6p+0f;   // float nearest sqrt 2
+// floats nearest 1/k! (k = 3..7) and 1/(2k+1) (k = 1..4)
+constexpr float kF3 = 0x1.555556p-3f, kF4 = 0x1.555556p-5f, kF5 = 0x1.111112p-7f,
+                kF6 = 0x1.6c16c2p-10f, kF7 = 0x1.a01a02p-13f;
+constexpr float kQ3 = 0x1.555556p-2f, kQ5 = 0x1.99999ap-3f, kQ7 = 0x1.24924ap-3f,
+                kQ9 = 0x1.c71c72p-4f;
+// Watson's density parameters as printed with Eq. (cone_retinal_density); r_m,
+// absent from the paper, is the cited formula's 41.03 deg.
+constexpr float kA = 0.9851f, kR2 = 1.058f, kRe = 22.14f, kRm = 41.03f;
+constexpr float kEccMax = 180.0f;           // eccentricity clamp, degrees
+constexpr float kPFloor = 0x1p-64f;         // rescale the bias product below this
+constexpr float kPScale = 0x1p64f;
+
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+
+// exp(x) for x <= 0: x = n ln2 + r, |r| <= ln2/2; Taylor series of exp(r) to
+// degree 7 in Horner form; times 2^n through the exponent field.
+__device__ __forceinline__ float exp_nonpos(float x) {
+  x = fminf(fmaxf(x, -87.0f), 0.0f);
+  const float n = rintf(fmul(x, kLog2e));
+  const float r = fsub(fsub(x, fmul(n, kLn2Hi)), fmul(n, kLn2Lo));
+  float p = kF7;
+  p = fadd(kF6, fmul(r, p));
+  p = fadd(kF5, fmul(r, p));
+  p = fadd(kF4, fmul(r, p));
+  p = fadd(kF3, fmul(r, p));
+  p = fadd(0.5f, fmul(r, p));
+  p = fadd(1.0f, fmul(r, p));
+  p = fadd(1.0f, fmul(r, p));
+  const int ni = __float2int_rn(n);
+  return fmul(p, __uint_as_float(static_cast<uint32_t>(ni + 127) << 23));
+}
+
+// ln(u) for normal u > 0: u = m 2^e, m in [sqrt(1/2), sqrt 2); ln m = 2 atanh(s),
+// s = (m-1)/(m+1), series in s^2 to s^8/9.
+__device__ __forceinline__ float log_pos(float u) {
+  const uint32_t b = __float_as_uint(u);
+  int e = static_cast<int>((b >> 23) & 0xffu) - 127;
+  float m = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
+  if (m > kSqrt2) {
+    m = fmul(m, 0.5f);
+    e += 1;
+  }
+  const float s = fdiv(fsub(m, 1.0f), fadd(m, 1.0f));
+  const float z = fmul(s, s);
+  float q = kQ9;
+  q = fadd(kQ7, fmul(z, q));
+  q = fadd(kQ5, fmul(z, q));
+  q = fadd(kQ3, fmul(z, q));
+  q = fadd(1.0f, fmul(z, q));
+  const float lnm = fmul(fmul(2.0f, s), q);
+  const float fe = __int2float_rn(e);
+  return fadd(fmul(fe, kLn2Hi), fadd(fmul(fe, kLn2Lo), lnm));
+}
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds, key bumped by the Weyl
+// constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint32_t word(const uint4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// top 24 bits, forced odd, scaled by 2^-24: exact and strictly inside (0, 1)
+__device__ __forceinline__ float unit_uniform(uint32_t x) {
+  return fmul(__uint2float_rn((x >> 8) | 1u), 0x1p-24f);
+}
+
+// d(e) / (2 d_c(0)) of Eq. (cone_retinal_density):
+//   ((a / (1+e/r_2)^2) + (1-a) exp(-e/r_e)) / (1 + e/r_m)
+__device__ __forceinline__ float density(float e) {
+  const float tm = fadd(1.0f, fdiv(e, kRm));
+  const float t2 = fadd(1.0f, fdiv(e, kR2));
+  const float a_term = fdiv(kA, fmul(t2, t2));
+  const float b_term = fmul(fsub(1.0f, kA), exp_nonpos(-fdiv(e, kRe)));
+  return fdiv(fadd(a_term, b_term), tm);
+}
+
+// ---------------------------------------------------------------- parameters
+
+struct StreamDev {
+  float* W;          // [plane]
+  float* P;          // [plane]
+  float* key;        // [K][plane]
+  uint32_t* idx;     // [K][plane]
+  float* wt;         // [K][plane]
+  void* col;         // [3][K][plane] float or __half
+  int64_t plane;     // entries per plane (multiple of 64)
+  int32_t width, height, K, hw;
+  float r_f;         // fovea radius, px
+  float delta;       // degrees per px
+  uint32_t seed_lo, seed_hi, stream_id;
+  int32_t bias;
+};
+
+struct FrameDev {
+  const float* frame;  // [H][pitch]
+  int64_t pitch;
+  const uint8_t* fov;  // [H][W] or null
+  float* out;          // [H][W][3] or null
+  float gx, gy;
+  uint32_t t;
+};
+
+// density at the fovea edge, the normaliser of Eq. (phat)
+__device__ __forceinline__ float fovea_density(const StreamDev& s) {
+  return density(fminf(fmul(s.r_f, s.delta), kEccMax));
+}
+
+// Eq. (phat) for one pixel centre; d_f = fovea_density(s).
+__device__ __forceinline__ float pixel_weight(const StreamDev& s, float d_f, int x, int y,
+                                              float gx, float gy) {
+  const float dx = fsub(fadd(__int2float_rn(x), 0.5f), gx);
+  const float dy = fsub(fadd(__int2float_rn(y), 0.5f), gy);
+  const float d = __fsqrt_rn(fadd(fmul(dx, dx), fmul(dy, dy)));
+  if (d <= s.r_f) return 1.0f;
+  const float e = fminf(fmul(d, s.delta), kEccMax);
+  return fminf(fdiv(density(e), d_f), 1.0f);
+}
+
+// ---------------------------------------------------------------- vector I/O
+
+template <int N> struct VecF;
+template <> struct VecF<1> { using T = float; };
+template <> struct VecF<2> { using T = float2; };
+template <> struct VecF<4> { using T = float4; };
+
+template <int N>
+__device__ __forceinline__ void load_f(const float* p, float (&v)[N]) {
+  typename VecF<N>::T t = *reinterpret_cast<const typename VecF<N>::T*>(p);
+  const float* tf = reinterpret_cast<const float*>(&t);
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = tf[i];
+}
+
+template <int N>
+__device__ __forceinline__ void store_f(float* p, const float (&v)[N]) {
+  typename VecF<N>::T t;
+  float* tf = reinterpret_cast<float*>(&t);
+#pragma unroll
+  for (int i = 0; i < N; ++i) tf[i] = v[i];
+  *reinterpret_cast<typename VecF<N>::T*>(p) = t;
+}
+
+template <int N> struct VecH;
+template <> struct VecH<1> { using T = unsigned short; };
+template <> struct VecH<2> { using T = unsigned int; };
+template <> struct VecH<4> { using T = uint2; };
+
+template <int N>
+__device__ __forceinline__ void load_h(const __half* p, float (&v)[N]) {
+  typename VecH<N>::T t = *reinterpret_cast<const typename VecH<N>::T*>(p);
+  const __half* th = reinterpret_cast<const __half*>(&t);
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = __half2float(th[i]);
+}
+
+template <bool F16, int N>
+__device__ __forceinline__ void load_colv(const void* base, int64_t off, float (&v)[N]) {
+  if constexpr (F16) load_h<N>(static_cast<const __half*>(base) + off, v);
+  else load_f<N>(static_cast<const float*>(base) + off, v);
+}
+
+template <bool F16>
+__device__ __forceinline__ void store_col(void* base, int64_t off, float v) {
+  if constexpr (F16) static_cast<__half*>(base)[off] = __float2half_rn(v);
+  else static_cast<float*>(base)[off] = v;
+}
+
+// colour as it will be stored in a slot (FP16 storage rounds to nearest even)
+template <bool F16>
+__device__ __forceinline__ float stored_colour(float c) {
+  if constexpr (F16) return __half2float(__float2half_rn(c));
+  else return c;
+}
+
+// ---------------------------------------------------------------- the pixel group
+
+// One thread's group of PX consecutive pixels p0 .. p0+PX-1 (p0 % PX == 0):
+// weight, key, bias, key race over the K slots, fused resolve, stores.
+// KT > 0 fixes K at compile time; KT == 0 reads s.K. VEC: the group lies in one
+// row and the frame/out rows are 16-byte friendly, so frame and out move as
+// vectors; otherwise each pixel is addressed on its own.
+template <int KT, bool F16, int PX, bool VEC>
+__device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f, int p0) {
+  const int K = KT > 0 ? KT : s.K;
+  const int64_t pl = s.plane;
+
+  bool valid[PX];
+  int xs[PX], ys[PX];
+  if constexpr (VEC) {
+    const int y = p0 / s.width;
+    const int x = p0 - y * s.width;
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+      valid[i] = true;
+      xs[i] = x + i;
+      ys[i] = y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+      const int p = p0 + i;
+      valid[i] = p < s.hw;
+      ys[i] = valid[i] ? p / s.width : 0;
+      xs[i] = valid[i] ? p - ys[i] * s.width : 0;
+    }
+  }
+
+  // incoming colours
+  float rgb[PX][3];
+  if constexpr (VEC) {
+    float v[3 * PX];
+    const float* src = f.frame + static_cast<int64_t>(ys[0]) * f.pitch + 3 * xs[0];
+    if constexpr (PX == 4) {
+      float a[4], b[4], c[4];
+      load_f<4>(src, a);
+      load_f<4>(src + 4, b);
+      load_f<4>(src + 8, c);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { v[i] = a[i]; v[4 + i] = b[i]; v[8 + i] = c[i]; }
+    } else if constexpr (PX == 2) {
+      float a[2], b[2], c[2];
+      load_f<2>(src, a);
+      load_f<2>(src + 2, b);
+      load_f<2>(src + 4, c);
+      v[0] = a[0]; v[1] = a[1]; v[2] = b[0]; v[3] = b[1]; v[4] = c[0]; v[5] = c[1];
+    } else {
+      v[0] = src[0]; v[1] = src[1]; v[2] = src[2];
+    }
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+      rgb[i][0] = v[3 * i]; rgb[i][1] = v[3 * i + 1]; rgb[i][2] = v[3 * i + 2];
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+      if (valid[i]) {
+        const float* src = f.frame + static_cast<int64_t>(ys[i]) * f.pitch + 3 * xs[i];
+        rgb[i][0] = src[0]; rgb[i][1] = src[1]; rgb[i][2] = src[2];
+      } else {
+        rgb[i][0] = rgb[i][1] = rgb[i][2] = 0.0f;
+      }
+    }
+  }
+
+  bool flush[PX];
+#pragma unroll
+  for (int i = 0; i < PX; ++i)
+    flush[i] = (f.fov != nullptr) && valid[i] && f.fov[p0 + i] == 0xFFu;
+
+  // uniforms: one Philox block per 4 consecutive pixels, word p mod 4 (PX divides
+  // 4 and p0 % PX == 0, so the group never straddles two blocks)
+  static_assert(4 % PX == 0, "pixels per thread must divide 4");
+  float u[PX];
+  {
+    const uint4 blk = philox4x32_10(
+        make_uint4(static_cast<uint32_t>(p0) >> 2, f.t, s.stream_id, 0u), s.seed_lo, s.seed_hi);
+#pragma unroll
+    for (int i = 0; i < PX; ++i) u[i] = unit_uniform(word(blk, (p0 + i) & 3));
+  }
+
+  // weight (Eq. phat) and A-ES key -ln(u)/w
+  const float d_f = fovea_density(s);
+  float w[PX], k[PX];
+#pragma unroll
+  for (int i = 0; i < PX; ++i) {
+    w[i] = valid[i] ? pixel_weight(s, d_f, xs[i], ys[i], f.gx, f.gy) : 1.0f;
+    k[i] = fdiv(-log_pos(u[i]), w[i]);
+  }
+
+  // Eq. (temporal-bias) on the history, then Alg. 2's sum
+  float Wv[PX], Pv[PX];
+  load_f<PX>(s.W + p0, Wv);
+  load_f<PX>(s.P + p0, Pv);
+  bool rescale[PX];
+  float ks[PX];
+#pragma unroll
+  for (int i = 0; i < PX; ++i) {
+    rescale[i] = false;
+    if (!valid[i]) { ks[i] = kInf; continue; }
+    if (flush[i]) { Wv[i] = 0.0f; Pv[i] = 1.0f; }
+    if (s.bias && Wv[i] > 0.0f) {
+      const float den = fadd(Wv[i], w[i]);
+      const float g = fdiv(w[i], den);
+      const float fb = fsub(1.0f, g);
+      Wv[i] = fmul(Wv[i], fb);
+      Pv[i] = fmul(Pv[i], fb);
+      if (Pv[i] < kPFloor) {
+        Pv[i] = fmul(Pv[i], kPScale);
+        rescale[i] = true;
+      }
+    }
+    Wv[i] = fadd(Wv[i], w[i]);
+    ks[i] = fmul(k[i], Pv[i]);
+  }
+
+  // key race: the slot holding the largest key (lowest index on ties; an empty
+  // slot holds +inf) is replaced iff the new key is strictly smaller
+  float kmax[PX];
+  int jm[PX];
+#pragma unroll
+  for (int i = 0; i < PX; ++i) { kmax[i] = -1.0f; jm[i] = 0; }
+#pragma unroll 8
+  for (int j = 0; j < K; ++j) {
+    float kv[PX];
+    load_f<PX>(s.key + j * pl + p0, kv);
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+      float kj = flush[i] ? kInf : kv[i];
+      if (rescale[i] && kj != kInf) kj = fminf(fmul(kj, kPScale), kFltMax);
+      if (kj > kmax[i]) { kmax[i] = kj; jm[i] = j; }
+    }
+  }
+  bool repl[PX];
+  float cst[PX][3];
+#pragma unroll
+  for (int i = 0; i < PX; ++i) {
+    repl[i] = valid[i] && ks[i] < kmax[i];
+    cst[i][0] = stored_colour<F16>(rgb[i][0]);
+    cst[i][1] = stored_colour<F16>(rgb[i][1]);
+    cst[i][2] = stored_colour<F16>(rgb[i][2]);
+  }
+
+  // fused resolve over the slots as they will be after this push
+  if (f.out != nullptr) {
+    float num[PX][3], den[PX];
+#pragma unroll
+    for (int i = 0; i < PX; ++i) { num[i][0] = num[i][1] = num[i][2] = 0.0f; den[i] = 0.0f; }
+#pragma unroll 4
+    for (int j = 0; j < K; ++j) {
+      float wv[PX], c0[PX], c1[PX], c2[PX];
+      load_f<PX>(s.wt + j * pl + p0, wv);
+      load_colv<F16, PX>(s.col, (0 * K + j) * pl + p0, c0);
+      load_colv<F16, PX>(s.col, (1 * K + j) * pl + p0, c1);
+      load_colv<F16, PX>(s.col, (2 * K + j) * pl + p0, c2);
+#pragma unroll
+      for (int i = 0; i < PX; ++i) {
+        float a = wv[i], r = c0[i], g = c1[i], b = c2[i];
+        if (flush[i]) { a = 0.0f; r = g = b = 0.0f; }
+        if (repl[i] && jm[i] == j) { a = w[i]; r = cst[i][0]; g = cst[i][1]; b = cst[i][2]; }
+        num[i][0] = __fmaf_rn(a, r, num[i][0]);
+        num[i][1] = __fmaf_rn(a, g, num[i][1]);
+        num[i][2] = __fmaf_rn(a, b, num[i][2]);
+        den[i] = fadd(den[i], a);
+      }
+    }
+    float o[PX][3];
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+      const float inv = den[i] > 0.0f ? __frcp_rn(den[i]) : 0.0f;
+      o[i][0] = fmul(num[i][0], inv);
+      o[i][1] = fmul(num[i][1], inv);
+      o[i][2] = fmul(num[i][2], inv);
+    }
+    if constexpr (VEC) {
+      float* dst = f.out + (static_cast<int64_t>(ys[0]) * s.width + xs[0]) * 3;
+      if constexpr (PX == 4) {
+        float a[4] = {o[0][0], o[0][1], o[0][2], o[1][0]};
+        float b[4] = {o[1][1], o[1][2], o[2][0], o[2][1]};
+        float c[4] = {o[2][2], o[3][0], o[3][1], o[3][2]};
+        store_f<4>(dst, a);
+        store_f<4>(dst + 4, b);
+        store_f<4>(dst + 8, c);
+      } else if constexpr (PX == 2) {
+        float a[2] = {o[0][0], o[0][1]};
+        float b[2] = {o[0][2], o[1][0]};
+        float c[2] = {o[1][1], o[1][2]};
+        store_f<2>(dst, a);
+        store_f<2>(dst + 2, b);
+        store_f<2>(dst + 4, c);
+      } else {
+        dst[0] = o[0][0]; dst[1] = o[0][1]; dst[2] = o[0][2];
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < PX; ++i) {
+        if (!valid[i]) continue;
+        float* dst = f.out + static_cast<int64_t>(p0 + i) * 3;
+        dst[0] = o[i][0]; dst[1] = o[i][1]; dst[2] = o[i][2];
+      }
+    }
+  }
+
+  // stores: running sums, the replaced slot, rescaled keys, flushed slots
+  store_f<PX>(s.W + p0, Wv);
+  store_f<PX>(s.P + p0, Pv);
+#pragma unroll
+  for (int i = 0; i < PX; ++i) {
+    if (!valid[i]) continue;
+    const int64_t p = p0 + i;
+    if (rescale[i] && !flush[i]) {
+      for (int j = 0; j < K; ++j) {
+        const float kj = s.key[j * pl + p];
+        if (kj != kInf) s.key[j * pl + p] = fminf(fmul(kj, kPScale), kFltMax);
+      }
+    }
+    if (flush[i]) {
+      for (int j = 0; j < K; ++j) {
+        if (j == jm[i]) continue;
+        s.key[j * pl + p] = kInf;
+        s.idx[j * pl + p] = kEmpty;
+        s.wt[j * pl + p] = 0.0f;
+        store_col<F16>(s.col, (0 * K + j) * pl + p, 0.0f);
+        store_col<F16>(s.col, (1 * K + j) * pl + p, 0.0f);
+        store_col<F16>(s.col, (2 * K + j) * pl + p, 0.0f);
+      }
+    }
+    if (repl[i]) {
+      const int j = jm[i];
+      s.key[j * pl + p] = ks[i];
+      s.idx[j * pl + p] = f.t;
+      s.wt[j * pl + p] = w[i];
+      store_col<F16>(s.col, (0 * K + j) * pl + p, rgb[i][0]);
+      store_col<F16>(s.col, (1 * K + j) * pl + p, rgb[i][1]);
+      store_col<F16>(s.col, (2 * K + j) * pl + p, rgb[i][2]);
+    }
+  }
+}
+
+// Standalone resolve of one group: the same accumulation as the fused resolve.
+template <int KT, bool F16, int PX>
+__device__ __forceinline__ void resolve_group(const StreamDev& s, float* out, int p0) {
+  const int K = KT > 0 ? KT : s.K;
+  const int64_t pl = s.plane;
+  float num[PX][3], den[PX];
+#pragma unroll
+  for (int i = 0; i < PX; ++i) { num[i][0] = num[i][1] = num[i][2] = 0.0f; den[i] = 0.0f; }
+#pragma unroll 4
+  for (int j = 0; j < K; ++j) {
+    float wv[PX], c0[PX], c1[PX], c2[PX];
+    load_f<PX>(s.wt + j * pl + p0, wv);
+    load_colv<F16, PX>(s.col, (0 * K + j) * pl + p0, c0);
+    load_colv<F16, PX>(s.col, (1 * K + j) * pl + p0, c1);
+    load_colv<F16, PX>(s.col, (2 * K + j) * pl + p0, c2);
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+      num[i][0] = __fmaf_rn(wv[i], c0[i], num[i][0]);
+      num[i][1] = __fmaf_rn(wv[i], c1[i], num[i][1]);
+      num[i][2] = __fmaf_rn(wv[i], c2[i], num[i][2]);
+      den[i] = fadd(den[i], wv[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < PX; ++i) {
+    if (p0 + i >= s.hw) continue;
+    const float inv = den[i] > 0.0f ? __frcp_rn(den[i]) : 0.0f;
+    float* dst = out + static_cast<int64_t>(p0 + i) * 3;
+    dst[0] = fmul(num[i][0], inv);
+    dst[1] = fmul(num[i][1], inv);
+    dst[2] = fmul(num[i][2], inv);
+  }
+}
+
+}  // namespace wrs

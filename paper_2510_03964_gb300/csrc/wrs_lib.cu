@@ -1,0 +1,411 @@
+// libwrs: C-ABI entry points (include/wrs.h) and the single-stream kernels.
+//
+// One kernel per frame does the whole per-pixel path of the paper (weight,
+// key, temporal bias, combine, resolve); see wrs_device.cuh for the
+// arithmetic. The host side only validates arguments, places the state planes
+// and picks a kernel instantiation.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "wrs.h"
+#include "wrs_device.cuh"
+#include "wrs_internal.h"
+
+using wrs::FrameDev;
+using wrs::StreamDev;
+
+// ---------------------------------------------------------------- errors
+
+static thread_local char g_err[512] = "";
+
+int wrs_fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+static void clear_error() { g_err[0] = '\0'; }
+
+extern "C" const char* wrs_last_error(void) { return g_err; }
+
+int wrs_cuda_fail(cudaError_t e, const char* what) {
+  return wrs_fail(WRS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------- config, layout
+
+static constexpr int64_t kPlaneAlign = 64;                 // entries; 256 B for 4-byte planes
+static constexpr int64_t kMaxPixels = (1ll << 31) - 64;
+
+int wrs_check_config(const wrs_config* c) {
+  if (!c) return wrs_fail(WRS_ERR_ARG, "config is NULL");
+  if (c->width < 1 || c->height < 1)
+    return wrs_fail(WRS_ERR_ARG, "width and height must be >= 1 (got %d x %d)", c->width,
+                    c->height);
+  if (static_cast<int64_t>(c->width) * c->height > kMaxPixels)
+    return wrs_fail(WRS_ERR_ARG, "width * height must be below 2^31 - 64");
+  if (c->K < 1 || c->K > WRS_MAX_K)
+    return wrs_fail(WRS_ERR_ARG, "K must be in 1..%d (got %d)", WRS_MAX_K, c->K);
+  if (!(c->fovea_radius_px > 0.0f) || !std::isfinite(c->fovea_radius_px))
+    return wrs_fail(WRS_ERR_ARG, "fovea_radius_px must be finite and > 0");
+  if (!std::isfinite(c->deg_per_px))
+    return wrs_fail(WRS_ERR_ARG, "deg_per_px must be finite");
+  if (c->color_fp16 != 0 && c->color_fp16 != 1)
+    return wrs_fail(WRS_ERR_ARG, "color_fp16 must be 0 or 1");
+  if (c->temporal_bias != 0 && c->temporal_bias != 1)
+    return wrs_fail(WRS_ERR_ARG, "temporal_bias must be 0 or 1");
+  return WRS_OK;
+}
+
+void wrs_make_layout(const wrs_config* c, wrs_layout* L) {
+  const int64_t hw = static_cast<int64_t>(c->width) * c->height;
+  const int64_t pl = (hw + kPlaneAlign - 1) / kPlaneAlign * kPlaneAlign;
+  L->plane_px = pl;
+  L->plane_bytes4 = pl * 4;
+  L->plane_bytes_col = pl * (c->color_fp16 ? 2 : 4);
+  L->W_off = 0;
+  L->P_off = L->W_off + L->plane_bytes4;
+  L->key_off = L->P_off + L->plane_bytes4;
+  L->idx_off = L->key_off + c->K * L->plane_bytes4;
+  L->wt_off = L->idx_off + c->K * L->plane_bytes4;
+  L->col_off = L->wt_off + c->K * L->plane_bytes4;
+  L->total_bytes = L->col_off + 3 * c->K * L->plane_bytes_col;
+}
+
+float wrs_delta(const wrs_config* c) {
+  // default: the fovea radius spans 2.5 degrees (IEEE single division)
+  return c->deg_per_px > 0.0f ? c->deg_per_px : 2.5f / c->fovea_radius_px;
+}
+
+StreamDev wrs_stream_dev(const wrs_ctx* x) {
+  StreamDev s;
+  uint8_t* b = x->state;
+  s.W = reinterpret_cast<float*>(b + x->lay.W_off);
+  s.P = reinterpret_cast<float*>(b + x->lay.P_off);
+  s.key = reinterpret_cast<float*>(b + x->lay.key_off);
+  s.idx = reinterpret_cast<uint32_t*>(b + x->lay.idx_off);
+  s.wt = reinterpret_cast<float*>(b + x->lay.wt_off);
+  s.col = b + x->lay.col_off;
+  s.plane = x->lay.plane_px;
+  s.width = x->cfg.width;
+  s.height = x->cfg.height;
+  s.K = x->cfg.K;
+  s.hw = x->cfg.width * x->cfg.height;
+  s.r_f = x->cfg.fovea_radius_px;
+  s.delta = wrs_delta(&x->cfg);
+  s.seed_lo = static_cast<uint32_t>(x->cfg.seed);
+  s.seed_hi = static_cast<uint32_t>(x->cfg.seed >> 32);
+  s.stream_id = x->cfg.stream_id;
+  s.bias = x->cfg.temporal_bias;
+  return s;
+}
+
+extern "C" size_t wrs_state_bytes(const wrs_config* cfg) {
+  if (wrs_check_config(cfg) != WRS_OK) return 0;
+  wrs_layout L;
+  wrs_make_layout(cfg, &L);
+  return static_cast<size_t>(L.total_bytes);
+}
+
+extern "C" int wrs_state_layout(const wrs_config* cfg, wrs_layout* out) {
+  if (!out) return wrs_fail(WRS_ERR_ARG, "layout output is NULL");
+  const int rc = wrs_check_config(cfg);
+  if (rc != WRS_OK) return rc;
+  wrs_make_layout(cfg, out);
+  return WRS_OK;
+}
+
+// ---------------------------------------------------------------- kernels
+
+namespace {
+
+// Every slot empty, W = 0, P = 1 (padding entries included).
+__global__ void init_kernel(StreamDev s) {
+  const int64_t n = s.plane;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += stride) {
+    s.W[i] = 0.0f;
+    s.P[i] = 1.0f;
+    for (int j = 0; j < s.K; ++j) {
+      s.key[j * n + i] = wrs::kInf;
+      s.idx[j * n + i] = wrs::kEmpty;
+      s.wt[j * n + i] = 0.0f;
+    }
+  }
+}
+
+__global__ void zero_kernel(uint8_t* p, int64_t bytes) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < bytes / 16;
+       i += stride)
+    reinterpret_cast<uint4*>(p)[i] = make_uint4(0, 0, 0, 0);
+}
+
+template <int KT, bool F16, int PX, bool VEC>
+__global__ void __launch_bounds__(256, PX == 4 ? 2 : 3) push_kernel(const __grid_constant__ StreamDev s,
+                                                      const __grid_constant__ FrameDev f) {
+  const int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t p0 = g * PX;
+  if (p0 >= s.hw) return;
+  wrs::push_group<KT, F16, PX, VEC>(s, f, static_cast<int>(p0));
+}
+
+template <int KT, bool F16, int PX>
+__global__ void __launch_bounds__(256, PX == 4 ? 2 : 3) resolve_kernel(const __grid_constant__ StreamDev s,
+                                                         float* __restrict__ out) {
+  const int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t p0 = g * PX;
+  if (p0 >= s.hw) return;
+  wrs::resolve_group<KT, F16, PX>(s, out, static_cast<int>(p0));
+}
+
+template <int KT, bool F16, int PX, bool VEC>
+cudaError_t launch_push_t(const StreamDev& s, const FrameDev& f, int block, cudaStream_t st) {
+  const int64_t groups = (static_cast<int64_t>(s.hw) + PX - 1) / PX;
+  const int64_t grid = (groups + block - 1) / block;
+  push_kernel<KT, F16, PX, VEC><<<static_cast<unsigned>(grid), block, 0, st>>>(s, f);
+  return cudaGetLastError();
+}
+
+template <int KT, bool F16>
+cudaError_t launch_push_px(const StreamDev& s, const FrameDev& f, int block, int px,
+                           cudaStream_t st) {
+  switch (px) {
+    case 4: return launch_push_t<KT, F16, 4, true>(s, f, block, st);
+    case 2: return launch_push_t<KT, F16, 2, true>(s, f, block, st);
+    default: return launch_push_t<KT, F16, 1, false>(s, f, block, st);
+  }
+}
+
+template <bool F16>
+cudaError_t launch_push_k(const StreamDev& s, const FrameDev& f, int block, int px,
+                          cudaStream_t st) {
+  switch (s.K) {
+    case 1: return launch_push_px<1, F16>(s, f, block, px, st);
+    case 2: return launch_push_px<2, F16>(s, f, block, px, st);
+    case 4: return launch_push_px<4, F16>(s, f, block, px, st);
+    case 8: return launch_push_px<8, F16>(s, f, block, px, st);
+    default: return launch_push_px<0, F16>(s, f, block, px, st);
+  }
+}
+
+template <int KT, bool F16, int PX>
+cudaError_t launch_resolve_t(const StreamDev& s, float* out, int block, cudaStream_t st) {
+  const int64_t groups = (static_cast<int64_t>(s.hw) + PX - 1) / PX;
+  const int64_t grid = (groups + block - 1) / block;
+  resolve_kernel<KT, F16, PX><<<static_cast<unsigned>(grid), block, 0, st>>>(s, out);
+  return cudaGetLastError();
+}
+
+template <bool F16>
+cudaError_t launch_resolve_k(const StreamDev& s, float* out, int block, int px,
+                             cudaStream_t st) {
+  const bool p4 = px == 4;
+  switch (s.K) {
+    case 1: return p4 ? launch_resolve_t<1, F16, 4>(s, out, block, st) : launch_resolve_t<1, F16, 1>(s, out, block, st);
+    case 2: return p4 ? launch_resolve_t<2, F16, 4>(s, out, block, st) : launch_resolve_t<2, F16, 1>(s, out, block, st);
+    case 4: return p4 ? launch_resolve_t<4, F16, 4>(s, out, block, st) : launch_resolve_t<4, F16, 1>(s, out, block, st);
+    case 8: return p4 ? launch_resolve_t<8, F16, 4>(s, out, block, st) : launch_resolve_t<8, F16, 1>(s, out, block, st);
+    default: return p4 ? launch_resolve_t<0, F16, 4>(s, out, block, st) : launch_resolve_t<0, F16, 1>(s, out, block, st);
+  }
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace
+
+// Pixels per thread that the frame/out pointers and the width allow, given the request.
+int wrs_effective_px(const wrs_ctx* x, const float* frame, int64_t pitch, const float* out) {
+  int px = x->px;
+  while (px > 1) {
+    const size_t a = px == 4 ? 16 : 8;
+    const bool ok = (x->cfg.width % px == 0) && (pitch % px == 0) && aligned(frame, a) &&
+                    (out == nullptr || aligned(out, a));
+    if (ok) break;
+    px /= 2;
+  }
+  return px;
+}
+
+cudaError_t wrs_launch_push(const StreamDev& s, const FrameDev& f, int block, int px,
+                            bool f16, cudaStream_t st) {
+  return f16 ? launch_push_k<true>(s, f, block, px, st)
+             : launch_push_k<false>(s, f, block, px, st);
+}
+
+// ---------------------------------------------------------------- C-ABI
+
+extern "C" int wrs_create(const wrs_config* cfg, void* d_state, size_t state_bytes,
+                          wrs_stream_t stream, wrs_ctx** out) {
+  clear_error();
+  if (!out) return wrs_fail(WRS_ERR_ARG, "output context pointer is NULL");
+  *out = nullptr;
+  int rc = wrs_check_config(cfg);
+  if (rc != WRS_OK) return rc;
+  if (!d_state) return wrs_fail(WRS_ERR_ARG, "d_state is NULL");
+  if (!aligned(d_state, 256)) return wrs_fail(WRS_ERR_ARG, "d_state must be 256-byte aligned");
+  wrs_layout L;
+  wrs_make_layout(cfg, &L);
+  if (state_bytes < static_cast<size_t>(L.total_bytes))
+    return wrs_fail(WRS_ERR_BUDGET, "state buffer holds %zu bytes, the stream needs %lld",
+                    state_bytes, static_cast<long long>(L.total_bytes));
+  wrs_ctx* x = new (std::nothrow) wrs_ctx;
+  if (!x) return wrs_fail(WRS_ERR_ARG, "out of host memory for the context");
+  x->cfg = *cfg;
+  x->lay = L;
+  x->state = static_cast<uint8_t*>(d_state);
+  x->t = 0;
+  x->block = kDefaultBlock;
+  x->px = kDefaultPx;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const StreamDev s = wrs_stream_dev(x);
+  // colour planes start zeroed; then the per-slot fields
+  const int64_t col_bytes = L.total_bytes - L.col_off;
+  zero_kernel<<<1216, 256, 0, st>>>(x->state + L.col_off, col_bytes);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    init_kernel<<<1216, 256, 0, st>>>(s);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    delete x;
+    return wrs_cuda_fail(e, "wrs_create: init launch");
+  }
+  *out = x;
+  return WRS_OK;
+}
+
+extern "C" int wrs_push_frame(wrs_ctx* x, const float* d_frame, int64_t pitch, float gx,
+                              float gy, const uint8_t* d_fov, float* d_out,
+                              wrs_stream_t stream) {
+  clear_error();
+  if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
+  if (!d_frame) return wrs_fail(WRS_ERR_ARG, "d_frame is NULL");
+  if (!aligned(d_frame, 4) || (d_out && !aligned(d_out, 4)))
+    return wrs_fail(WRS_ERR_ARG, "frame and out must be 4-byte aligned");
+  if (pitch < 3 * static_cast<int64_t>(x->cfg.width))
+    return wrs_fail(WRS_ERR_ARG, "frame_pitch_elems %lld is below 3 * width",
+                    static_cast<long long>(pitch));
+  if (!std::isfinite(gx) || !std::isfinite(gy))
+    return wrs_fail(WRS_ERR_ARG, "gaze must be finite");
+  if (x->t == 0xFFFFFFFFu) return wrs_fail(WRS_ERR_STATE, "frame counter exhausted");
+  const StreamDev s = wrs_stream_dev(x);
+  FrameDev f;
+  f.frame = d_frame;
+  f.pitch = pitch;
+  f.fov = d_fov;
+  f.out = d_out;
+  f.gx = gx;
+  f.gy = gy;
+  f.t = x->t;
+  const int px = wrs_effective_px(x, d_frame, pitch, d_out);
+  const cudaError_t e = wrs_launch_push(s, f, x->block, px, x->cfg.color_fp16 != 0,
+                                        static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_frame: launch");
+  x->t += 1;
+  return WRS_OK;
+}
+
+extern "C" int wrs_resolve(wrs_ctx* x, float* d_out, wrs_stream_t stream) {
+  clear_error();
+  if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
+  if (!d_out || !aligned(d_out, 4)) return wrs_fail(WRS_ERR_ARG, "d_out is NULL or unaligned");
+  const StreamDev s = wrs_stream_dev(x);
+  const int px = (x->px == 4) ? 4 : 1;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const cudaError_t e = x->cfg.color_fp16 ? launch_resolve_k<true>(s, d_out, x->block, px, st)
+                                          : launch_resolve_k<false>(s, d_out, x->block, px, st);
+  if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_resolve: launch");
+  return WRS_OK;
+}
+
+extern "C" int wrs_destroy(wrs_ctx* x) {
+  clear_error();
+  delete x;
+  return WRS_OK;
+}
+
+extern "C" int wrs_push_frame_host(wrs_ctx* x, const float* h_frame, float gx, float gy,
+                                   const uint8_t* h_fov, float* h_out, float* d_frame_stage,
+                                   uint8_t* d_fov_stage, float* d_out_stage,
+                                   wrs_stream_t stream) {
+  clear_error();
+  if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
+  if (!h_frame || !h_out || !d_frame_stage || !d_out_stage)
+    return wrs_fail(WRS_ERR_ARG, "frame, out and their staging buffers must be non-NULL");
+  if (h_fov && !d_fov_stage) return wrs_fail(WRS_ERR_ARG, "h_fov_map needs d_fov_stage");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t hw = static_cast<size_t>(x->cfg.width) * x->cfg.height;
+  cudaError_t e = cudaMemcpyAsync(d_frame_stage, h_frame, hw * 3 * sizeof(float),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && h_fov)
+    e = cudaMemcpyAsync(d_fov_stage, h_fov, hw, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_frame_host: upload");
+  const int rc = wrs_push_frame(x, d_frame_stage, 3 * static_cast<int64_t>(x->cfg.width), gx,
+                                gy, h_fov ? d_fov_stage : nullptr, d_out_stage, stream);
+  if (rc != WRS_OK) return rc;
+  e = cudaMemcpyAsync(h_out, d_out_stage, hw * 3 * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_frame_host: download");
+  return WRS_OK;
+}
+
+extern "C" int wrs_export_state(wrs_ctx* x, void* h_dst, size_t bytes, wrs_stream_t stream) {
+  clear_error();
+  if (!x || !h_dst) return wrs_fail(WRS_ERR_ARG, "context or destination is NULL");
+  if (bytes < static_cast<size_t>(x->lay.total_bytes))
+    return wrs_fail(WRS_ERR_BUDGET, "destination holds %zu bytes, the state is %lld", bytes,
+                    static_cast<long long>(x->lay.total_bytes));
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(h_dst, x->state, x->lay.total_bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_export_state");
+  return WRS_OK;
+}
+
+extern "C" int wrs_import_state(wrs_ctx* x, const void* h_src, size_t bytes,
+                                uint32_t frame_index, wrs_stream_t stream) {
+  clear_error();
+  if (!x || !h_src) return wrs_fail(WRS_ERR_ARG, "context or source is NULL");
+  if (bytes < static_cast<size_t>(x->lay.total_bytes))
+    return wrs_fail(WRS_ERR_BUDGET, "source holds %zu bytes, the state is %lld", bytes,
+                    static_cast<long long>(x->lay.total_bytes));
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(x->state, h_src, x->lay.total_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_import_state");
+  x->t = frame_index;
+  return WRS_OK;
+}
+
+extern "C" uint32_t wrs_frame_index(const wrs_ctx* x) { return x ? x->t : 0u; }
+
+extern "C" int wrs_set_launch(wrs_ctx* x, int block_threads, int px_per_thread) {
+  clear_error();
+  if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
+  if (block_threads == 0) block_threads = kDefaultBlock;
+  if (px_per_thread == 0) px_per_thread = kDefaultPx;
+  if (block_threads < 64 || block_threads > 256 || block_threads % 32 != 0)
+    return wrs_fail(WRS_ERR_ARG, "block_threads must be a multiple of 32 in 64..256");
+  if (px_per_thread != 1 && px_per_thread != 2 && px_per_thread != 4)
+    return wrs_fail(WRS_ERR_ARG, "px_per_thread must be 1, 2 or 4");
+  x->block = block_threads;
+  x->px = px_per_thread;
+  return WRS_OK;
+}
+
+extern "C" int wrs_get_launch(const wrs_ctx* x, int* block_threads, int* px_per_thread) {
+  if (!x || !block_threads || !px_per_thread)
+    return wrs_fail(WRS_ERR_ARG, "NULL argument");
+  *block_threads = x->block;
+  *px_per_thread = x->px;
+  return WRS_OK;
+}

@@ -1,0 +1,173 @@
+"""Python face of libwrs: the same calls as include/wrs.h, with torch tensors
+for device memory and torch CUDA streams. Every step of the reservoir update
+and resolve runs in the library's CUDA kernels; this module only passes
+pointers, sizes and stream handles.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from ._lib import (WRS_EMPTY_SLOT, WrsConfig, WrsError, WrsLayout, check, load)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev_ptr(t: torch.Tensor | None, dtype, name: str):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def make_config(width, height, K, fovea_radius_px, deg_per_px=0.0, seed=0, stream_id=0,
+                color_fp16=False, temporal_bias=True) -> WrsConfig:
+    return WrsConfig(int(width), int(height), int(K), float(fovea_radius_px), float(deg_per_px),
+                     int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream_id) & 0xFFFFFFFF,
+                     1 if color_fp16 else 0, 1 if temporal_bias else 0)
+
+
+def state_bytes(cfg: WrsConfig) -> int:
+    n = load().wrs_state_bytes(C.byref(cfg))
+    if n == 0:
+        raise WrsError(1, load().wrs_last_error().decode())
+    return int(n)
+
+
+def state_layout(cfg: WrsConfig) -> WrsLayout:
+    lay = WrsLayout()
+    check(load().wrs_state_layout(C.byref(cfg), C.byref(lay)))
+    return lay
+
+
+class Stream:
+    """One frame stream's reservoirs, resident in a caller-visible torch buffer.
+
+    ``state`` may be passed in (uint8 CUDA tensor of at least
+    ``state_bytes(cfg)`` bytes, 256-byte aligned) so that callers, such as the
+    serving pool, control placement; otherwise one is allocated.
+    """
+
+    def __init__(self, width, height, K, fovea_radius_px, deg_per_px=0.0, seed=0, stream_id=0,
+                 color_fp16=False, temporal_bias=True, device=None, stream=None,
+                 state: torch.Tensor | None = None):
+        self.cfg = make_config(width, height, K, fovea_radius_px, deg_per_px, seed, stream_id,
+                               color_fp16, temporal_bias)
+        self.width, self.height, self.K = int(width), int(height), int(K)
+        self.color_fp16 = bool(color_fp16)
+        self.nbytes = state_bytes(self.cfg)
+        self.layout = state_layout(self.cfg)
+        if state is None:
+            dev = torch.device("cuda") if device is None else torch.device(device)
+            state = torch.empty(self.nbytes, dtype=torch.uint8, device=dev)
+        elif state.numel() < self.nbytes:
+            raise ValueError("state buffer too small")
+        self.state = state
+        self.device = state.device
+        ctx = C.c_void_p()
+        with torch.cuda.device(self.device):
+            check(load().wrs_create(C.byref(self.cfg), state.data_ptr(), state.numel(),
+                                    _stream_handle(stream), C.byref(ctx)))
+        self._ctx = ctx
+
+    # -- the four core calls -------------------------------------------------
+    def push_frame(self, frame: torch.Tensor, gaze, fov_map: torch.Tensor | None = None,
+                   out: torch.Tensor | None = None, stream=None, pitch: int | None = None):
+        """frame: float32 CUDA [H][W][3] (or [H][pitch] with ``pitch``)."""
+        if pitch is None:
+            if tuple(frame.shape[-3:]) != (self.height, self.width, 3) or not frame.is_contiguous():
+                raise ValueError("frame must be a contiguous [H][W][3] float32 tensor")
+            pitch = 3 * self.width
+        check(load().wrs_push_frame(self._ctx, _dev_ptr(frame, torch.float32, "frame"), int(pitch),
+                                    float(gaze[0]), float(gaze[1]),
+                                    _dev_ptr(fov_map, torch.uint8, "fov_map"),
+                                    _dev_ptr(out, torch.float32, "out"), _stream_handle(stream)))
+        return out
+
+    def resolve(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.height, self.width, 3), dtype=torch.float32, device=self.device)
+        check(load().wrs_resolve(self._ctx, _dev_ptr(out, torch.float32, "out"), _stream_handle(stream)))
+        return out
+
+    def close(self):
+        if self._ctx:
+            load().wrs_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- extras ----------------------------------------------------------------
+    @property
+    def frame_index(self) -> int:
+        return int(load().wrs_frame_index(self._ctx))
+
+    def set_launch(self, block_threads: int = 0, px_per_thread: int = 0):
+        check(load().wrs_set_launch(self._ctx, int(block_threads), int(px_per_thread)))
+
+    def get_launch(self):
+        b, p = C.c_int(), C.c_int()
+        check(load().wrs_get_launch(self._ctx, C.byref(b), C.byref(p)))
+        return b.value, p.value
+
+    def push_frame_host(self, h_frame: torch.Tensor, gaze, h_out: torch.Tensor, d_frame_stage,
+                        d_out_stage, h_fov_map=None, d_fov_stage=None, stream=None):
+        """Host frame in, host resolved frame out (copies inside the call)."""
+        for t, n in ((h_frame, "h_frame"), (h_out, "h_out")):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"{n} must be a contiguous host tensor")
+        check(load().wrs_push_frame_host(
+            self._ctx, h_frame.data_ptr(), float(gaze[0]), float(gaze[1]),
+            None if h_fov_map is None else h_fov_map.data_ptr(), h_out.data_ptr(),
+            _dev_ptr(d_frame_stage, torch.float32, "d_frame_stage"),
+            _dev_ptr(d_fov_stage, torch.uint8, "d_fov_stage"),
+            _dev_ptr(d_out_stage, torch.float32, "d_out_stage"), _stream_handle(stream)))
+
+    def export_raw(self, stream=None) -> np.ndarray:
+        buf = np.empty(self.nbytes, dtype=np.uint8)
+        check(load().wrs_export_state(self._ctx, buf.ctypes.data, buf.nbytes, _stream_handle(stream)))
+        return buf
+
+    def import_raw(self, buf: np.ndarray, frame_index: int, stream=None):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        check(load().wrs_import_state(self._ctx, buf.ctypes.data, buf.nbytes, int(frame_index),
+                                      _stream_handle(stream)))
+
+    def export_state(self, stream=None) -> dict:
+        """State planes as numpy arrays: W [HW], P [HW], key/idx/wt [K][HW], col [3][K][HW]."""
+        return unpack_state(self.export_raw(stream), self.layout, self.K, self.width * self.height,
+                            self.color_fp16)
+
+
+def unpack_state(buf: np.ndarray, lay: WrsLayout, K: int, hw: int, color_fp16: bool) -> dict:
+    pl = lay.plane_px
+
+    def plane(off, dtype, n):
+        return np.frombuffer(buf, dtype=dtype, count=n * pl, offset=off).reshape(n, pl)[:, :hw]
+
+    cdt = np.float16 if color_fp16 else np.float32
+    return {
+        "W": plane(lay.W_off, np.float32, 1)[0].copy(),
+        "P": plane(lay.P_off, np.float32, 1)[0].copy(),
+        "key": plane(lay.key_off, np.float32, K).copy(),
+        "idx": plane(lay.idx_off, np.uint32, K).copy(),
+        "wt": plane(lay.wt_off, np.float32, K).copy(),
+        "col": plane(lay.col_off, cdt, 3 * K).reshape(3, K, hw).copy(),
+    }
+
+
+__all__ = ["Stream", "make_config", "state_bytes", "state_layout", "unpack_state", "WrsError",
+           "WRS_EMPTY_SLOT"]

@@ -18,8 +18,8 @@ scenes and its Tobii recordings, Sec. 5).
 """
 from .configs import WORKLOADS, Workload, StreamSpec, workload
 from .images import ground_truth, box_pyramid
-from .foveate import Foveator
+from .foveate import Foveator, frame_pixels
 from .gaze import gaze_path
 
 __all__ = ["WORKLOADS", "Workload", "StreamSpec", "workload", "ground_truth",
-           "box_pyramid", "Foveator", "gaze_path"]
+           "box_pyramid", "Foveator", "frame_pixels", "gaze_path"]

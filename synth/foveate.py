@@ -70,3 +70,18 @@ class Foveator:
             fr[t] = a.cpu().numpy()
             fm[t] = b.cpu().numpy()
         return fr, fm
+
+
+def frame_pixels(fv: Foveator, gx: float, gy: float, pix: torch.Tensor) -> torch.Tensor:
+    """Colours of the listed pixels (int64 row-major indices) of fv.frame(gx, gy),
+    float32 [n][3], computed for those pixels only (same float64 ring test)."""
+    pix = pix.to(fv.device)
+    ys = torch.div(pix, fv.width, rounding_mode="floor")
+    xs = pix - ys * fv.width
+    dx = (xs.to(torch.float64) + 0.5) - float(gx)
+    dy = (ys.to(torch.float64) + 0.5) - float(gy)
+    d2 = dx * dx + dy * dy
+    lev = torch.zeros_like(pix)
+    for r2 in fv._r2:
+        lev += (d2 > r2).to(torch.int64)
+    return fv._pyr.index_select(0, lev * (fv.height * fv.width) + pix)

@@ -1,0 +1,79 @@
+"""The C-ABI library loads and exports what include/wrs.h declares; host-side
+argument checks reject bad input before any CUDA call (no GPU needed)."""
+import ctypes as C
+
+import pytest
+
+import paper_2510_03964_gb300 as pkg
+from paper_2510_03964_gb300 import _lib
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return pkg.load()
+
+
+def test_every_declared_function_is_exported(lib):
+    names = pkg.header_functions()
+    assert {"wrs_create", "wrs_push_frame", "wrs_resolve", "wrs_destroy"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/wrs.h but not exported"
+    # the binding declares exactly the header's functions
+    assert set(_lib.SIGNATURES) >= set(names)
+
+
+def test_header_constants_match_binding():
+    text = open(_lib.HEADER).read()
+    assert "#define WRS_MAX_K 16" in text
+    assert "#define WRS_EMPTY_SLOT 0xFFFFFFFFu" in text
+    for i, n in enumerate(["WRS_OK", "WRS_ERR_ARG", "WRS_ERR_CUDA", "WRS_ERR_BUDGET",
+                           "WRS_ERR_TIMEOUT", "WRS_ERR_STATE"]):
+        assert f"#define {n} {i}" in text
+
+
+def test_state_bytes_and_layout(lib):
+    cfg = pkg.make_config(3840, 2160, 8, 200.0)
+    n = pkg.state_bytes(cfg)
+    lay = pkg.state_layout(cfg)
+    hw = 3840 * 2160
+    assert lay.plane_px % 64 == 0 and lay.plane_px >= hw
+    assert n == lay.total_bytes == lay.plane_px * 4 * (2 + 3 * 8) + lay.plane_px * 4 * 3 * 8
+    for off in (lay.W_off, lay.P_off, lay.key_off, lay.idx_off, lay.wt_off, lay.col_off):
+        assert off % 256 == 0
+    cfg16 = pkg.make_config(3840, 2160, 8, 200.0, color_fp16=True)
+    assert pkg.state_bytes(cfg16) == lay.plane_px * (4 * (2 + 3 * 8) + 2 * 3 * 8)
+    # ragged size: planes padded to 64 entries
+    lay2 = pkg.state_layout(pkg.make_config(37, 23, 3, 5.0))
+    assert lay2.plane_px == 896
+
+
+@pytest.mark.parametrize("bad", [dict(width=0), dict(height=-1), dict(K=0), dict(K=17),
+                                 dict(fovea_radius_px=0.0), dict(fovea_radius_px=float("inf")),
+                                 dict(deg_per_px=float("nan")), dict(width=1 << 16, height=1 << 15)])
+def test_invalid_configs_rejected(lib, bad):
+    args = dict(width=64, height=64, K=4, fovea_radius_px=8.0)
+    args.update(bad)
+    cfg = pkg.make_config(**args)
+    assert lib.wrs_state_bytes(C.byref(cfg)) == 0
+    assert lib.wrs_last_error().decode() != ""
+    ctx = C.c_void_p()
+    rc = lib.wrs_create(C.byref(cfg), C.c_void_p(256), 1 << 30, None, C.byref(ctx))
+    assert rc == _lib.WRS_ERR_ARG and not ctx.value
+
+
+def test_create_checks_buffer_before_cuda(lib):
+    cfg = pkg.make_config(64, 64, 4, 8.0)
+    ctx = C.c_void_p()
+    assert lib.wrs_create(C.byref(cfg), None, 1 << 20, None, C.byref(ctx)) == _lib.WRS_ERR_ARG
+    assert lib.wrs_create(C.byref(cfg), C.c_void_p(256 + 16), 1 << 20, None, C.byref(ctx)) == _lib.WRS_ERR_ARG
+    assert "aligned" in lib.wrs_last_error().decode()
+    need = lib.wrs_state_bytes(C.byref(cfg))
+    assert lib.wrs_create(C.byref(cfg), C.c_void_p(256), need - 1, None, C.byref(ctx)) == _lib.WRS_ERR_BUDGET
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    assert lib.wrs_push_frame(None, None, 0, 0.0, 0.0, None, None, None) == _lib.WRS_ERR_ARG
+    assert lib.wrs_resolve(None, None, None) == _lib.WRS_ERR_ARG
+    assert lib.wrs_destroy(None) == _lib.WRS_OK
+    assert lib.wrs_frame_index(None) == 0
+    assert lib.wrs_set_launch(None, 128, 4) == _lib.WRS_ERR_ARG
