@@ -255,8 +255,9 @@ def run_ours(args, world, rank, local):
     gaze = gaze_path(spec.width, spec.height, spec.frames, seed=seed, model=spec.gaze_model,
                      jitter_px=spec.jitter_px)
     hw = spec.width * spec.height
-    frames = torch.empty((spec.frames, spec.height, spec.width, 3), dtype=torch.float32, device=dev)
-    for t in range(spec.frames):
+    nfr = min(spec.frames, args.distinct_frames) if args.distinct_frames > 0 else spec.frames
+    frames = torch.empty((nfr, spec.height, spec.width, 3), dtype=torch.float32, device=dev)
+    for t in range(nfr):
         fv.frame(float(gaze[t, 0]), float(gaze[t, 1]), out=frames[t])
     out = torch.empty((spec.height, spec.width, 3), dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
@@ -268,7 +269,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
 
     def push(t):
-        st.push_frame(frames[t % spec.frames], gaze[t % spec.frames], None, out, stream=stream)
+        st.push_frame(frames[t % nfr], gaze[t % nfr], None, out, stream=stream)
 
     with torch.cuda.stream(stream):
         for t in range(args.warmup):
@@ -298,7 +299,7 @@ def run_ours(args, world, rank, local):
     # end-to-end through the host-buffer entry point (copies inside the timed region)
     e2e = None
     if args.e2e_steps > 0:
-        pool = min(spec.frames, 8)
+        pool = min(nfr, 8)
         h_frames = torch.empty((pool, spec.height, spec.width, 3), dtype=torch.float32, pin_memory=True)
         for i in range(pool):
             h_frames[i].copy_(frames[i])
@@ -333,11 +334,14 @@ def run_ours(args, world, rank, local):
     bpp = algorithmic_bytes_per_px(spec.K, spec.color_fp16)
     achieved = bpp * hw / (kernel_avg * 1e-3) / 1e9
     kname = f"push_kernel<K={spec.K},{'fp16' if spec.color_fp16 else 'fp32'}>"
+    cfg = workload_config(spec, args.workload)
+    if nfr != spec.frames:
+        cfg["frames_distinct"] = nfr
     line = {
         "metric": METRIC, "value": round(ms_frame, 4), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": workload_config(spec, args.workload),
+        "data": "synthetic", "config": cfg,
         "mpx_updates_per_s": round(hw * world / (ms_frame * 1e-3) / 1e6, 1),
         "kernel_ms_avg": round(kernel_avg, 4),
         "kernel_ms_median": round(statistics.median(kernel_ms), 4),
@@ -371,6 +375,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="4k", choices=["4k", "4k_fp16", "hd"])
+    ap.add_argument("--distinct-frames", type=int, default=0,
+                    help="frames resident in HBM (default: all of the workload's)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--px", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=200)
