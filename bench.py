@@ -358,11 +358,11 @@ def run_ours(args, world, rank, local):
     if args.cpu_baseline:
         nthreads = os.cpu_count() or 1
         pixels = sample_pixels(spec, args.cpu_sample)
-        ms_cpu, nfr = oracle_ms_per_frame(spec, pixels, spec.frames, nthreads, fv, gaze,
+        ms_cpu, n_cpu_frames = oracle_ms_per_frame(spec, pixels, spec.frames, nthreads, fv, gaze,
                                           budget_s=args.cpu_budget_s)
         line["cpu_baseline"] = {
             "value": round(ms_cpu, 3), "unit": UNIT, "cores": nthreads, "kind": "oracle",
-            "sample": f"{len(pixels)} of {hw} pixels (every {hw // len(pixels)}th), {nfr} frames, "
+            "sample": f"{len(pixels)} of {hw} pixels (every {hw // len(pixels)}th), {n_cpu_frames} frames, "
                       f"mean of frames 1.. scaled to a full frame; oracle threads over pixels"}
     st.close()
     print(json.dumps(line), flush=True)
