@@ -266,6 +266,8 @@ def run_ours(args, world, rank, local):
                     stream=stream)
     if args.block or args.px:
         st.set_launch(args.block, args.px)
+    if args.pipe_px or args.pipe_stages or not args.pipe:
+        st.set_pipeline(bool(args.pipe), args.pipe_px, args.pipe_stages)
     torch.cuda.synchronize()
 
     def push(t):
@@ -333,8 +335,13 @@ def run_ours(args, world, rank, local):
     peaks = measured_peaks()
     bpp = algorithmic_bytes_per_px(spec.K, spec.color_fp16)
     achieved = bpp * hw / (kernel_avg * 1e-3) / 1e9
-    kname = f"push_kernel<K={spec.K},{'fp16' if spec.color_fp16 else 'fp32'}>"
+    kname = (f"{'pipe_kernel' if st.get_pipeline()[0] else 'push_kernel'}"
+             f"<K={spec.K},{'fp16' if spec.color_fp16 else 'fp32'}>")
     cfg = workload_config(spec, args.workload)
+    pipe_on, pipe_px, pipe_st = st.get_pipeline()
+    blk, px = st.get_launch()
+    cfg["kernel"] = (f"pipelined: {pipe_px} px/thread, tile {256 * pipe_px} px, {pipe_st} stages"
+                     if pipe_on else f"plain: block {blk}, {px} px/thread")
     if nfr != spec.frames:
         cfg["frames_distinct"] = nfr
     line = {
@@ -377,6 +384,9 @@ def main():
     ap.add_argument("--workload", default="4k", choices=["4k", "4k_fp16", "hd"])
     ap.add_argument("--distinct-frames", type=int, default=0,
                     help="frames resident in HBM (default: all of the workload's)")
+    ap.add_argument("--pipe", type=int, default=1, help="1: pipelined kernel (default), 0: plain")
+    ap.add_argument("--pipe-px", type=int, default=0)
+    ap.add_argument("--pipe-stages", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--px", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=200)

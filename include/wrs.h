@@ -83,6 +83,7 @@ typedef struct {
   int64_t plane_px;
   int64_t plane_bytes4;     /* plane_px * 4 */
   int64_t plane_bytes_col;  /* plane_px * 4 (FP32 colour) or * 2 (FP16 colour) */
+  int64_t status_off;       /* uint32 status word (WRS_OK or WRS_ERR_TIMEOUT), 256-byte header */
   int64_t W_off, P_off, key_off, idx_off, wt_off, col_off;
   int64_t total_bytes;
 } wrs_layout;
@@ -155,6 +156,29 @@ uint32_t wrs_frame_index(const wrs_ctx* ctx);
  * the kernel falls back to per-pixel frame access. */
 int wrs_set_launch(wrs_ctx* ctx, int block_threads, int px_per_thread);
 int wrs_get_launch(const wrs_ctx* ctx, int* block_threads, int* px_per_thread);
+
+/* Kernel choice for wrs_push_frame. enable = 1 (default) uses the pipelined
+ * persistent kernel whenever width % 4 == 0, frame_pitch_elems == 3 * width and
+ * frame/out are 16-byte aligned (else the plain kernel runs): one CTA per SM
+ * streams tiles of 256 * px_per_thread pixels through `stages` shared-memory
+ * stages with bulk asynchronous copies. 0 for px_per_thread / stages picks the
+ * widest tile with two stages and as many stages as fit. Results are
+ * bit-identical across every choice. WRS_ERR_ARG if the stages do not fit in
+ * shared memory. */
+int wrs_set_pipeline(wrs_ctx* ctx, int enable, int px_per_thread, int stages);
+int wrs_get_pipeline(const wrs_ctx* ctx, int* enable, int* px_per_thread, int* stages);
+
+/* Every device-side wait (the pipelined kernel's copy barriers) gives up after
+ * timeout_ns (0: the 2 s default) and records WRS_ERR_TIMEOUT in the stream's
+ * status word instead of hanging. test_extra_tx > 0 makes each wait expect
+ * that many bytes more than are copied, so that it runs out: fault injection
+ * for tests only (<= 4096). */
+int wrs_set_wait_limit(wrs_ctx* ctx, uint64_t timeout_ns, uint32_t test_extra_tx);
+
+/* Waits for `stream`, reads and clears the status word. WRS_OK, or
+ * WRS_ERR_TIMEOUT if a wait gave up since the last check (the frames pushed
+ * meanwhile may be partly applied). */
+int wrs_check_status(wrs_ctx* ctx, wrs_stream_t stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* wrs_last_error(void);

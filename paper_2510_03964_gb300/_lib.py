@@ -22,9 +22,9 @@ class WrsConfig(C.Structure):
 
 class WrsLayout(C.Structure):
     _fields_ = [("plane_px", C.c_int64), ("plane_bytes4", C.c_int64), ("plane_bytes_col", C.c_int64),
-                ("W_off", C.c_int64), ("P_off", C.c_int64), ("key_off", C.c_int64),
-                ("idx_off", C.c_int64), ("wt_off", C.c_int64), ("col_off", C.c_int64),
-                ("total_bytes", C.c_int64)]
+                ("status_off", C.c_int64), ("W_off", C.c_int64), ("P_off", C.c_int64),
+                ("key_off", C.c_int64), ("idx_off", C.c_int64), ("wt_off", C.c_int64),
+                ("col_off", C.c_int64), ("total_bytes", C.c_int64)]
 
 
 _V = C.c_void_p
@@ -42,6 +42,10 @@ SIGNATURES = {
     "wrs_frame_index": (C.c_uint32, [_V]),
     "wrs_set_launch": (_I, [_V, _I, _I]),
     "wrs_get_launch": (_I, [_V, C.POINTER(_I), C.POINTER(_I)]),
+    "wrs_set_pipeline": (_I, [_V, _I, _I, _I]),
+    "wrs_get_pipeline": (_I, [_V, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "wrs_set_wait_limit": (_I, [_V, C.c_uint64, C.c_uint32]),
+    "wrs_check_status": (_I, [_V, _V]),
     "wrs_last_error": (C.c_char_p, []),
 }
 

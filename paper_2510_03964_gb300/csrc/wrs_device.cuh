@@ -218,17 +218,126 @@ __device__ __forceinline__ float stored_colour(float c) {
   else return c;
 }
 
+// ---------------------------------------------------------------- per-pixel steps
+
+// Eq. (temporal-bias) on the history, then Alg. 2's sum. Returns the race key
+// k * P of the new candidate; `rescale` reports a 2^64 rescale of P (the
+// stored keys must then be rescaled by the same factor).
+__device__ __forceinline__ float bias_and_sum(int bias, float w, float k, float& W, float& P,
+                                              bool& rescale) {
+  rescale = false;
+  if (bias && W > 0.0f) {
+    const float den = fadd(W, w);
+    const float g = fdiv(w, den);
+    const float fb = fsub(1.0f, g);
+    W = fmul(W, fb);
+    P = fmul(P, fb);
+    if (P < kPFloor) {
+      P = fmul(P, kPScale);
+      rescale = true;
+    }
+  }
+  W = fadd(W, w);
+  return fmul(k, P);
+}
+
+// stored key as the race sees it this frame (after a flush or a rescale)
+__device__ __forceinline__ float race_key(float kv, bool flush, bool rescale) {
+  float kj = flush ? kInf : kv;
+  if (rescale && kj != kInf) kj = fminf(fmul(kj, kPScale), kFltMax);
+  return kj;
+}
+
+// Where one group's reservoir planes are read from: global memory (plane
+// stride = plane entries, index = pixel) or a shared-memory tile (stride = tile
+// entries, index = position in the tile). `frame` points at the group's first
+// RGB triple when the group's colours are contiguous, else is null.
+struct Src {
+  const float* W;
+  const float* P;
+  const float* key;
+  const float* wt;
+  const void* col;
+  int64_t stride;
+  int64_t at;
+  const float* frame;
+};
+
+__device__ __forceinline__ Src global_src(const StreamDev& s, const FrameDev& f, int p0, bool vec) {
+  Src r;
+  r.W = s.W; r.P = s.P; r.key = s.key; r.wt = s.wt; r.col = s.col;
+  r.stride = s.plane;
+  r.at = p0;
+  r.frame = nullptr;
+  if (vec) {
+    const int y = p0 / s.width;
+    const int x = p0 - y * s.width;
+    r.frame = f.frame + static_cast<int64_t>(y) * f.pitch + 3 * x;
+  }
+  return r;
+}
+
+template <int N>
+__device__ __forceinline__ void load_rgb(const float* src, float (&rgb)[N][3]) {
+  float v[3 * N];
+  if constexpr (N == 4) {
+    float a[4], b[4], c[4];
+    load_f<4>(src, a);
+    load_f<4>(src + 4, b);
+    load_f<4>(src + 8, c);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { v[i] = a[i]; v[4 + i] = b[i]; v[8 + i] = c[i]; }
+  } else if constexpr (N == 2) {
+    float a[2], b[2], c[2];
+    load_f<2>(src, a);
+    load_f<2>(src + 2, b);
+    load_f<2>(src + 4, c);
+    v[0] = a[0]; v[1] = a[1]; v[2] = b[0]; v[3] = b[1]; v[4] = c[0]; v[5] = c[1];
+  } else {
+    v[0] = src[0]; v[1] = src[1]; v[2] = src[2];
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    rgb[i][0] = v[3 * i]; rgb[i][1] = v[3 * i + 1]; rgb[i][2] = v[3 * i + 2];
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void store_rgb(float* dst, const float (&o)[N][3]) {
+  if constexpr (N == 4) {
+    float a[4] = {o[0][0], o[0][1], o[0][2], o[1][0]};
+    float b[4] = {o[1][1], o[1][2], o[2][0], o[2][1]};
+    float c[4] = {o[2][2], o[3][0], o[3][1], o[3][2]};
+    store_f<4>(dst, a);
+    store_f<4>(dst + 4, b);
+    store_f<4>(dst + 8, c);
+  } else if constexpr (N == 2) {
+    float a[2] = {o[0][0], o[0][1]};
+    float b[2] = {o[0][2], o[1][0]};
+    float c[2] = {o[1][1], o[1][2]};
+    store_f<2>(dst, a);
+    store_f<2>(dst + 2, b);
+    store_f<2>(dst + 4, c);
+  } else {
+    dst[0] = o[0][0]; dst[1] = o[0][1]; dst[2] = o[0][2];
+  }
+}
+
 // ---------------------------------------------------------------- the pixel group
 
 // One thread's group of PX consecutive pixels p0 .. p0+PX-1 (p0 % PX == 0):
-// weight, key, bias, key race over the K slots, fused resolve, stores.
-// KT > 0 fixes K at compile time; KT == 0 reads s.K. VEC: the group lies in one
-// row and the frame/out rows are 16-byte friendly, so frame and out move as
-// vectors; otherwise each pixel is addressed on its own.
+// weight, key, bias, key race over the K slots, fused resolve, stores. Reads
+// the reservoir through `src` (global planes or a shared-memory tile); writes
+// always go to the global planes. KT > 0 fixes K at compile time. VEC: the
+// group lies in one row and src.frame / f.out take vector accesses; otherwise
+// every pixel is addressed on its own (and may lie past the end of the image).
 template <int KT, bool F16, int PX, bool VEC>
-__device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f, int p0) {
+__device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f, int p0,
+                                           const Src& src, float d_f) {
   const int K = KT > 0 ? KT : s.K;
   const int64_t pl = s.plane;
+  const int64_t ss = src.stride;
+  const int64_t sa = src.at;
 
   bool valid[PX];
   int xs[PX], ys[PX];
@@ -254,34 +363,14 @@ __device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f
   // incoming colours
   float rgb[PX][3];
   if constexpr (VEC) {
-    float v[3 * PX];
-    const float* src = f.frame + static_cast<int64_t>(ys[0]) * f.pitch + 3 * xs[0];
-    if constexpr (PX == 4) {
-      float a[4], b[4], c[4];
-      load_f<4>(src, a);
-      load_f<4>(src + 4, b);
-      load_f<4>(src + 8, c);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) { v[i] = a[i]; v[4 + i] = b[i]; v[8 + i] = c[i]; }
-    } else if constexpr (PX == 2) {
-      float a[2], b[2], c[2];
-      load_f<2>(src, a);
-      load_f<2>(src + 2, b);
-      load_f<2>(src + 4, c);
-      v[0] = a[0]; v[1] = a[1]; v[2] = b[0]; v[3] = b[1]; v[4] = c[0]; v[5] = c[1];
-    } else {
-      v[0] = src[0]; v[1] = src[1]; v[2] = src[2];
-    }
-#pragma unroll
-    for (int i = 0; i < PX; ++i) {
-      rgb[i][0] = v[3 * i]; rgb[i][1] = v[3 * i + 1]; rgb[i][2] = v[3 * i + 2];
-    }
+    load_rgb<PX>(src.frame, rgb);
   } else {
 #pragma unroll
     for (int i = 0; i < PX; ++i) {
       if (valid[i]) {
-        const float* src = f.frame + static_cast<int64_t>(ys[i]) * f.pitch + 3 * xs[i];
-        rgb[i][0] = src[0]; rgb[i][1] = src[1]; rgb[i][2] = src[2];
+        const float* fp = src.frame ? src.frame + 3 * i
+                                    : f.frame + static_cast<int64_t>(ys[i]) * f.pitch + 3 * xs[i];
+        rgb[i][0] = fp[0]; rgb[i][1] = fp[1]; rgb[i][2] = fp[2];
       } else {
         rgb[i][0] = rgb[i][1] = rgb[i][2] = 0.0f;
       }
@@ -305,7 +394,6 @@ __device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f
   }
 
   // weight (Eq. phat) and A-ES key -ln(u)/w
-  const float d_f = fovea_density(s);
   float w[PX], k[PX];
 #pragma unroll
   for (int i = 0; i < PX; ++i) {
@@ -315,8 +403,8 @@ __device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f
 
   // Eq. (temporal-bias) on the history, then Alg. 2's sum
   float Wv[PX], Pv[PX];
-  load_f<PX>(s.W + p0, Wv);
-  load_f<PX>(s.P + p0, Pv);
+  load_f<PX>(src.W + sa, Wv);
+  load_f<PX>(src.P + sa, Pv);
   bool rescale[PX];
   float ks[PX];
 #pragma unroll
@@ -324,19 +412,7 @@ __device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f
     rescale[i] = false;
     if (!valid[i]) { ks[i] = kInf; continue; }
     if (flush[i]) { Wv[i] = 0.0f; Pv[i] = 1.0f; }
-    if (s.bias && Wv[i] > 0.0f) {
-      const float den = fadd(Wv[i], w[i]);
-      const float g = fdiv(w[i], den);
-      const float fb = fsub(1.0f, g);
-      Wv[i] = fmul(Wv[i], fb);
-      Pv[i] = fmul(Pv[i], fb);
-      if (Pv[i] < kPFloor) {
-        Pv[i] = fmul(Pv[i], kPScale);
-        rescale[i] = true;
-      }
-    }
-    Wv[i] = fadd(Wv[i], w[i]);
-    ks[i] = fmul(k[i], Pv[i]);
+    ks[i] = bias_and_sum(s.bias, w[i], k[i], Wv[i], Pv[i], rescale[i]);
   }
 
   // key race: the slot holding the largest key (lowest index on ties; an empty
@@ -348,11 +424,10 @@ __device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f
 #pragma unroll 8
   for (int j = 0; j < K; ++j) {
     float kv[PX];
-    load_f<PX>(s.key + j * pl + p0, kv);
+    load_f<PX>(src.key + j * ss + sa, kv);
 #pragma unroll
     for (int i = 0; i < PX; ++i) {
-      float kj = flush[i] ? kInf : kv[i];
-      if (rescale[i] && kj != kInf) kj = fminf(fmul(kj, kPScale), kFltMax);
+      const float kj = race_key(kv[i], flush[i], rescale[i]);
       if (kj > kmax[i]) { kmax[i] = kj; jm[i] = j; }
     }
   }
@@ -374,10 +449,10 @@ __device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f
 #pragma unroll 4
     for (int j = 0; j < K; ++j) {
       float wv[PX], c0[PX], c1[PX], c2[PX];
-      load_f<PX>(s.wt + j * pl + p0, wv);
-      load_colv<F16, PX>(s.col, (0 * K + j) * pl + p0, c0);
-      load_colv<F16, PX>(s.col, (1 * K + j) * pl + p0, c1);
-      load_colv<F16, PX>(s.col, (2 * K + j) * pl + p0, c2);
+      load_f<PX>(src.wt + j * ss + sa, wv);
+      load_colv<F16, PX>(src.col, (0 * K + j) * ss + sa, c0);
+      load_colv<F16, PX>(src.col, (1 * K + j) * ss + sa, c1);
+      load_colv<F16, PX>(src.col, (2 * K + j) * ss + sa, c2);
 #pragma unroll
       for (int i = 0; i < PX; ++i) {
         float a = wv[i], r = c0[i], g = c1[i], b = c2[i];
@@ -398,24 +473,7 @@ __device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f
       o[i][2] = fmul(num[i][2], inv);
     }
     if constexpr (VEC) {
-      float* dst = f.out + (static_cast<int64_t>(ys[0]) * s.width + xs[0]) * 3;
-      if constexpr (PX == 4) {
-        float a[4] = {o[0][0], o[0][1], o[0][2], o[1][0]};
-        float b[4] = {o[1][1], o[1][2], o[2][0], o[2][1]};
-        float c[4] = {o[2][2], o[3][0], o[3][1], o[3][2]};
-        store_f<4>(dst, a);
-        store_f<4>(dst + 4, b);
-        store_f<4>(dst + 8, c);
-      } else if constexpr (PX == 2) {
-        float a[2] = {o[0][0], o[0][1]};
-        float b[2] = {o[0][2], o[1][0]};
-        float c[2] = {o[1][1], o[1][2]};
-        store_f<2>(dst, a);
-        store_f<2>(dst + 2, b);
-        store_f<2>(dst + 4, c);
-      } else {
-        dst[0] = o[0][0]; dst[1] = o[0][1]; dst[2] = o[0][2];
-      }
+      store_rgb<PX>(f.out + (static_cast<int64_t>(ys[0]) * s.width + xs[0]) * 3, o);
     } else {
 #pragma unroll
       for (int i = 0; i < PX; ++i) {
@@ -435,7 +493,7 @@ __device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f
     const int64_t p = p0 + i;
     if (rescale[i] && !flush[i]) {
       for (int j = 0; j < K; ++j) {
-        const float kj = s.key[j * pl + p];
+        const float kj = src.key[j * ss + sa + i];
         if (kj != kInf) s.key[j * pl + p] = fminf(fmul(kj, kPScale), kFltMax);
       }
     }

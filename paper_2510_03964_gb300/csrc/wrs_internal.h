@@ -9,14 +9,31 @@
 struct wrs_ctx {
   wrs_config cfg;
   wrs_layout lay;
-  uint8_t* state;  // caller-owned device buffer
-  uint32_t t;      // frames pushed
-  int block;       // threads per block of the fused kernel
-  int px;          // requested pixels per thread
+  uint8_t* state;        // caller-owned device buffer
+  uint32_t t;            // frames pushed
+  int block;             // threads per block of the plain kernel
+  int px;                // requested pixels per thread of the plain kernel
+  int device;            // CUDA device the state lives on
+  int sms;               // its multiprocessor count
+  int pipe;              // 1: use the pipelined kernel when the frame allows it
+  int pipe_px;           // pipelined kernel: pixels per thread (tile = 256 * px)
+  int pipe_stages;       // pipelined kernel: shared-memory stages
+  uint64_t timeout_ns;   // bound on every device-side wait
+  uint32_t test_extra_tx;  // > 0 only to exercise the timeout path in tests
 };
 
 constexpr int kDefaultBlock = 256;
 constexpr int kDefaultPx = 4;
+constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;  // 2 s
+constexpr size_t kSmemBudget = 227 * 1024 - 1024;       // dynamic shared memory per CTA we use
+
+uint32_t* wrs_status_word(const wrs_ctx* x);
+size_t wrs_pipe_stage_bytes(int K, bool f16, int px, bool resolve);
+bool wrs_pipe_supported(const wrs_ctx* x, const float* frame, int64_t pitch, const float* out);
+cudaError_t wrs_launch_pipe(const wrs::StreamDev& s, const wrs::FrameDev& f, bool f16, int px,
+                            int stages, int sms, uint32_t* status, uint64_t timeout_ns,
+                            uint32_t extra_tx, cudaStream_t st);
+void wrs_default_pipe(int K, bool f16, int* px, int* stages);
 
 int wrs_fail(int code, const char* fmt, ...);
 int wrs_cuda_fail(cudaError_t e, const char* what);

@@ -43,6 +43,7 @@ int wrs_cuda_fail(cudaError_t e, const char* what) {
 
 static constexpr int64_t kPlaneAlign = 64;                 // entries; 256 B for 4-byte planes
 static constexpr int64_t kMaxPixels = (1ll << 31) - 64;
+static constexpr int64_t kStatusBytes = 256;                // status header before the planes
 
 int wrs_check_config(const wrs_config* c) {
   if (!c) return wrs_fail(WRS_ERR_ARG, "config is NULL");
@@ -70,7 +71,8 @@ void wrs_make_layout(const wrs_config* c, wrs_layout* L) {
   L->plane_px = pl;
   L->plane_bytes4 = pl * 4;
   L->plane_bytes_col = pl * (c->color_fp16 ? 2 : 4);
-  L->W_off = 0;
+  L->status_off = 0;
+  L->W_off = kStatusBytes;
   L->P_off = L->W_off + L->plane_bytes4;
   L->key_off = L->P_off + L->plane_bytes4;
   L->idx_off = L->key_off + c->K * L->plane_bytes4;
@@ -105,6 +107,22 @@ StreamDev wrs_stream_dev(const wrs_ctx* x) {
   s.stream_id = x->cfg.stream_id;
   s.bias = x->cfg.temporal_bias;
   return s;
+}
+
+uint32_t* wrs_status_word(const wrs_ctx* x) {
+  return reinterpret_cast<uint32_t*>(x->state + x->lay.status_off);
+}
+
+void wrs_default_pipe(int K, bool f16, int* px, int* stages) {
+  // widest tile that still leaves room for two stages, then as many stages as fit (<= 4)
+  int p = 4;
+  while (p > 1 && 2 * wrs_pipe_stage_bytes(K, f16, p, true) + 64 > kSmemBudget) p /= 2;
+  size_t per = wrs_pipe_stage_bytes(K, f16, p, true);
+  int st = static_cast<int>(kSmemBudget / (per + 8));
+  if (st > 4) st = 4;
+  if (st < 1) st = 1;
+  *px = p;
+  *stages = st;
 }
 
 extern "C" size_t wrs_state_bytes(const wrs_config* cfg) {
@@ -155,7 +173,9 @@ __global__ void __launch_bounds__(256, PX == 4 ? 2 : 3) push_kernel(const __grid
   const int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   const int64_t p0 = g * PX;
   if (p0 >= s.hw) return;
-  wrs::push_group<KT, F16, PX, VEC>(s, f, static_cast<int>(p0));
+  const float d_f = wrs::fovea_density(s);
+  wrs::push_group<KT, F16, PX, VEC>(s, f, static_cast<int>(p0),
+                                    wrs::global_src(s, f, static_cast<int>(p0), VEC), d_f);
 }
 
 template <int KT, bool F16, int PX>
@@ -265,12 +285,27 @@ extern "C" int wrs_create(const wrs_config* cfg, void* d_state, size_t state_byt
   x->t = 0;
   x->block = kDefaultBlock;
   x->px = kDefaultPx;
+  x->pipe = 1;
+  wrs_default_pipe(cfg->K, cfg->color_fp16 != 0, &x->pipe_px, &x->pipe_stages);
+  x->timeout_ns = kDefaultTimeoutNs;
+  x->test_extra_tx = 0;
+  cudaError_t e = cudaGetDevice(&x->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, x->device);
+  if (e != cudaSuccess) {
+    delete x;
+    return wrs_cuda_fail(e, "wrs_create: device query");
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const StreamDev s = wrs_stream_dev(x);
-  // colour planes start zeroed; then the per-slot fields
+  // status word and colour planes start zeroed; then the per-slot fields
+  zero_kernel<<<1, 32, 0, st>>>(x->state + L.status_off, kStatusBytes);
+  e = cudaGetLastError();
   const int64_t col_bytes = L.total_bytes - L.col_off;
-  zero_kernel<<<1216, 256, 0, st>>>(x->state + L.col_off, col_bytes);
-  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    zero_kernel<<<1216, 256, 0, st>>>(x->state + L.col_off, col_bytes);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) {
     init_kernel<<<1216, 256, 0, st>>>(s);
     e = cudaGetLastError();
@@ -306,9 +341,16 @@ extern "C" int wrs_push_frame(wrs_ctx* x, const float* d_frame, int64_t pitch, f
   f.gx = gx;
   f.gy = gy;
   f.t = x->t;
-  const int px = wrs_effective_px(x, d_frame, pitch, d_out);
-  const cudaError_t e = wrs_launch_push(s, f, x->block, px, x->cfg.color_fp16 != 0,
-                                        static_cast<cudaStream_t>(stream));
+  cudaError_t e;
+  if (x->pipe && wrs_pipe_supported(x, d_frame, pitch, d_out)) {
+    e = wrs_launch_pipe(s, f, x->cfg.color_fp16 != 0, x->pipe_px, x->pipe_stages, x->sms,
+                        wrs_status_word(x), x->timeout_ns, x->test_extra_tx,
+                        static_cast<cudaStream_t>(stream));
+  } else {
+    const int px = wrs_effective_px(x, d_frame, pitch, d_out);
+    e = wrs_launch_push(s, f, x->block, px, x->cfg.color_fp16 != 0,
+                        static_cast<cudaStream_t>(stream));
+  }
   if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_frame: launch");
   x->t += 1;
   return WRS_OK;
@@ -408,4 +450,66 @@ extern "C" int wrs_get_launch(const wrs_ctx* x, int* block_threads, int* px_per_
   *block_threads = x->block;
   *px_per_thread = x->px;
   return WRS_OK;
+}
+
+extern "C" int wrs_set_pipeline(wrs_ctx* x, int enable, int px_per_thread, int stages) {
+  clear_error();
+  if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
+  int dpx, dst;
+  wrs_default_pipe(x->cfg.K, x->cfg.color_fp16 != 0, &dpx, &dst);
+  if (px_per_thread == 0) px_per_thread = dpx;
+  if (px_per_thread != 1 && px_per_thread != 2 && px_per_thread != 4)
+    return wrs_fail(WRS_ERR_ARG, "px_per_thread must be 1, 2 or 4");
+  if (stages == 0) {
+    const size_t per = wrs_pipe_stage_bytes(x->cfg.K, x->cfg.color_fp16 != 0, px_per_thread, true);
+    stages = static_cast<int>(kSmemBudget / (per + 8));
+    if (stages > 4) stages = 4;
+  }
+  if (stages < 1 || stages > 8) return wrs_fail(WRS_ERR_ARG, "stages must be in 1..8");
+  const size_t need = stages * (wrs_pipe_stage_bytes(x->cfg.K, x->cfg.color_fp16 != 0,
+                                                     px_per_thread, true) + 8);
+  if (enable && need > kSmemBudget)
+    return wrs_fail(WRS_ERR_ARG, "%d stages of %d px/thread need %zu B of shared memory (> %zu)",
+                    stages, px_per_thread, need, kSmemBudget);
+  x->pipe = enable ? 1 : 0;
+  x->pipe_px = px_per_thread;
+  x->pipe_stages = stages;
+  return WRS_OK;
+}
+
+extern "C" int wrs_get_pipeline(const wrs_ctx* x, int* enable, int* px_per_thread, int* stages) {
+  if (!x || !enable || !px_per_thread || !stages) return wrs_fail(WRS_ERR_ARG, "NULL argument");
+  *enable = x->pipe;
+  *px_per_thread = x->pipe_px;
+  *stages = x->pipe_stages;
+  return WRS_OK;
+}
+
+extern "C" int wrs_set_wait_limit(wrs_ctx* x, uint64_t timeout_ns, uint32_t test_extra_tx) {
+  clear_error();
+  if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
+  if (timeout_ns == 0) timeout_ns = kDefaultTimeoutNs;
+  if (timeout_ns > 60ull * 1000000000ull) return wrs_fail(WRS_ERR_ARG, "timeout above 60 s");
+  if (test_extra_tx > 4096) return wrs_fail(WRS_ERR_ARG, "test_extra_tx above 4096");
+  x->timeout_ns = timeout_ns;
+  x->test_extra_tx = test_extra_tx;
+  return WRS_OK;
+}
+
+extern "C" int wrs_check_status(wrs_ctx* x, wrs_stream_t stream) {
+  clear_error();
+  if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t word = 0;
+  cudaError_t e = cudaMemcpyAsync(&word, wrs_status_word(x), sizeof word, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_check_status");
+  if (word == WRS_OK) return WRS_OK;
+  e = cudaMemsetAsync(wrs_status_word(x), 0, sizeof word, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_check_status: clear");
+  return wrs_fail(static_cast<int>(word),
+                  "a device-side wait gave up after %llu ns; frames pushed since the last check "
+                  "may be incomplete",
+                  static_cast<unsigned long long>(x->timeout_ns));
 }

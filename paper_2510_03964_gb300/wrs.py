@@ -123,6 +123,21 @@ class Stream:
         check(load().wrs_get_launch(self._ctx, C.byref(b), C.byref(p)))
         return b.value, p.value
 
+    def set_pipeline(self, enable: bool = True, px_per_thread: int = 0, stages: int = 0):
+        check(load().wrs_set_pipeline(self._ctx, 1 if enable else 0, int(px_per_thread), int(stages)))
+
+    def get_pipeline(self):
+        e, p, s = C.c_int(), C.c_int(), C.c_int()
+        check(load().wrs_get_pipeline(self._ctx, C.byref(e), C.byref(p), C.byref(s)))
+        return bool(e.value), p.value, s.value
+
+    def set_wait_limit(self, timeout_ns: int = 0, test_extra_tx: int = 0):
+        check(load().wrs_set_wait_limit(self._ctx, int(timeout_ns), int(test_extra_tx)))
+
+    def check_status(self, stream=None) -> int:
+        """Waits for the stream; returns 0, or the status code a device-side wait recorded."""
+        return int(load().wrs_check_status(self._ctx, _stream_handle(stream)))
+
     def push_frame_host(self, h_frame: torch.Tensor, gaze, h_out: torch.Tensor, d_frame_stage,
                         d_out_stage, h_fov_map=None, d_fov_stage=None, stream=None):
         """Host frame in, host resolved frame out (copies inside the call)."""

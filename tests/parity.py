@@ -79,7 +79,7 @@ class PairedRun:
     def __init__(self, width, height, K, r_f, radii=None, frames=8, seed=0, stream_id=0,
                  gaze_model="jitter", jitter_px=4.0, color_fp16=False, temporal_bias=True,
                  deg_per_px=0.0, pixels=None, launch=None, gaze=None, scene_seed=None,
-                 frame_device="cpu"):
+                 frame_device="cpu", pipeline=None):
         self.width, self.height, self.K = width, height, K
         self.color_fp16 = color_fp16
         self.dev = torch.device("cuda")
@@ -95,6 +95,8 @@ class PairedRun:
                               temporal_bias=temporal_bias, device=self.dev)
         if launch:
             self.gpu.set_launch(*launch)
+        if pipeline is not None:
+            self.gpu.set_pipeline(*pipeline)
         self.orc = oracle.OracleStream(width, height, K, r_f, deg_per_px=deg_per_px, seed=seed,
                                        stream_id=stream_id, temporal_bias=temporal_bias,
                                        pixels=self.pixels, nthreads=8)

@@ -37,11 +37,12 @@ def test_state_bytes_and_layout(lib):
     lay = pkg.state_layout(cfg)
     hw = 3840 * 2160
     assert lay.plane_px % 64 == 0 and lay.plane_px >= hw
-    assert n == lay.total_bytes == lay.plane_px * 4 * (2 + 3 * 8) + lay.plane_px * 4 * 3 * 8
+    assert n == lay.total_bytes == 256 + lay.plane_px * 4 * (2 + 3 * 8) + lay.plane_px * 4 * 3 * 8
+    assert lay.status_off == 0
     for off in (lay.W_off, lay.P_off, lay.key_off, lay.idx_off, lay.wt_off, lay.col_off):
         assert off % 256 == 0
     cfg16 = pkg.make_config(3840, 2160, 8, 200.0, color_fp16=True)
-    assert pkg.state_bytes(cfg16) == lay.plane_px * (4 * (2 + 3 * 8) + 2 * 3 * 8)
+    assert pkg.state_bytes(cfg16) == 256 + lay.plane_px * (4 * (2 + 3 * 8) + 2 * 3 * 8)
     # ragged size: planes padded to 64 entries
     lay2 = pkg.state_layout(pkg.make_config(37, 23, 3, 5.0))
     assert lay2.plane_px == 896
