@@ -266,8 +266,8 @@ def run_ours(args, world, rank, local):
                     stream=stream)
     if args.block or args.px:
         st.set_launch(args.block, args.px)
-    if args.pipe_px or args.pipe_stages or not args.pipe:
-        st.set_pipeline(bool(args.pipe), args.pipe_px, args.pipe_stages)
+    if args.pipe_px or args.pipe_stages or args.pipe_ctas or not args.pipe:
+        st.set_pipeline(bool(args.pipe), args.pipe_px, args.pipe_stages, args.pipe_ctas)
     torch.cuda.synchronize()
 
     def push(t):
@@ -338,9 +338,10 @@ def run_ours(args, world, rank, local):
     kname = (f"{'pipe_kernel' if st.get_pipeline()[0] else 'push_kernel'}"
              f"<K={spec.K},{'fp16' if spec.color_fp16 else 'fp32'}>")
     cfg = workload_config(spec, args.workload)
-    pipe_on, pipe_px, pipe_st = st.get_pipeline()
+    pipe_on, pipe_px, pipe_st, pipe_ctas = st.get_pipeline()
     blk, px = st.get_launch()
-    cfg["kernel"] = (f"pipelined: {pipe_px} px/thread, tile {256 * pipe_px} px, {pipe_st} stages"
+    cfg["kernel"] = (f"pipelined: {pipe_px} px/thread, tile {256 * pipe_px} px, {pipe_st} stages, "
+                     f"{pipe_ctas or 'max'} CTAs/SM"
                      if pipe_on else f"plain: block {blk}, {px} px/thread")
     if nfr != spec.frames:
         cfg["frames_distinct"] = nfr
@@ -387,6 +388,7 @@ def main():
     ap.add_argument("--pipe", type=int, default=1, help="1: pipelined kernel (default), 0: plain")
     ap.add_argument("--pipe-px", type=int, default=0)
     ap.add_argument("--pipe-stages", type=int, default=0)
+    ap.add_argument("--pipe-ctas", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--px", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=200)

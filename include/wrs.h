@@ -159,14 +159,15 @@ int wrs_get_launch(const wrs_ctx* ctx, int* block_threads, int* px_per_thread);
 
 /* Kernel choice for wrs_push_frame. enable = 1 (default) uses the pipelined
  * persistent kernel whenever width % 4 == 0, frame_pitch_elems == 3 * width and
- * frame/out are 16-byte aligned (else the plain kernel runs): one CTA per SM
- * streams tiles of 256 * px_per_thread pixels through `stages` shared-memory
- * stages with bulk asynchronous copies. 0 for px_per_thread / stages picks the
- * widest tile with two stages and as many stages as fit. Results are
- * bit-identical across every choice. WRS_ERR_ARG if the stages do not fit in
- * shared memory. */
-int wrs_set_pipeline(wrs_ctx* ctx, int enable, int px_per_thread, int stages);
-int wrs_get_pipeline(const wrs_ctx* ctx, int* enable, int* px_per_thread, int* stages);
+ * frame/out are 16-byte aligned (else the plain kernel runs): persistent CTAs
+ * (ctas_per_sm per SM; 0 = as many as registers and shared memory allow)
+ * stream tiles of 256 * px_per_thread pixels (1, 2 or 4) through `stages`
+ * shared-memory stages with bulk asynchronous copies. 0 for px_per_thread /
+ * stages selects 256-pixel tiles and two stages. Results are bit-identical
+ * across every choice. WRS_ERR_ARG if the stages do not fit in shared memory. */
+int wrs_set_pipeline(wrs_ctx* ctx, int enable, int px_per_thread, int stages, int ctas_per_sm);
+int wrs_get_pipeline(const wrs_ctx* ctx, int* enable, int* px_per_thread, int* stages,
+                     int* ctas_per_sm);
 
 /* Every device-side wait (the pipelined kernel's copy barriers) gives up after
  * timeout_ns (0: the 2 s default) and records WRS_ERR_TIMEOUT in the stream's

@@ -4,7 +4,8 @@
  *
  * Build: gcc -std=c11 -O2 -ffp-contract=off (no fast-math). Every float
  * expression below is evaluated as written, one IEEE round-to-nearest-even
- * operation at a time, with no fused multiply-add.
+ * operation at a time; the only fused multiply-adds are the explicit fmaf
+ * calls (one rounding each), never contracted ones.
  *
  * Paper references are to "Enhancing Foveated Rendering with Weighted
  * Reservoir Sampling" (arXiv 2510.03964):
@@ -42,22 +43,23 @@ static float scale_pow2(float p, int n) {
 
 float orc_exp(float x) {
   /* exp(x) = 2^n exp(r), n = rint(x / ln 2), r = x - n ln 2 in [-ln2/2, ln2/2].
-   * exp(r) by its Taylor series to r^7/7! (truncation < 2^-27 relative).
+   * exp(r) by its Taylor series to r^7/7! (truncation < 2^-27 relative), in
+   * Horner form with fused multiply-adds (fmaf: one IEEE rounding each).
    * Coefficients are the floats nearest to 1/k!. */
   if (x < -87.0f) x = -87.0f;
   if (x > 0.0f) x = 0.0f;
   float n = rintf(x * LOG2E);
-  float r = (x - n * LN2_HI) - n * LN2_LO;
+  float r = fmaf(-n, LN2_HI, x);
+  r = fmaf(-n, LN2_LO, r);
   const float c2 = 1.0f / 2.0f, c3 = 1.0f / 6.0f, c4 = 1.0f / 24.0f, c5 = 1.0f / 120.0f,
               c6 = 1.0f / 720.0f, c7 = 1.0f / 5040.0f;
-  float p = c7;
-  p = c6 + r * p;
-  p = c5 + r * p;
-  p = c4 + r * p;
-  p = c3 + r * p;
-  p = c2 + r * p;
-  p = 1.0f + r * p;
-  p = 1.0f + r * p;
+  float p = fmaf(r, c7, c6);
+  p = fmaf(r, p, c5);
+  p = fmaf(r, p, c4);
+  p = fmaf(r, p, c3);
+  p = fmaf(r, p, c2);
+  p = fmaf(r, p, 1.0f);
+  p = fmaf(r, p, 1.0f);
   return scale_pow2(p, (int)n);
 }
 
@@ -78,14 +80,13 @@ float orc_log(float u) {
   float s = (m - 1.0f) / (m + 1.0f);
   float z = s * s;
   const float q3 = 1.0f / 3.0f, q5 = 1.0f / 5.0f, q7 = 1.0f / 7.0f, q9 = 1.0f / 9.0f;
-  float q = q9;
-  q = q7 + z * q;
-  q = q5 + z * q;
-  q = q3 + z * q;
-  q = 1.0f + z * q;
+  float q = fmaf(z, q9, q7);
+  q = fmaf(z, q, q5);
+  q = fmaf(z, q, q3);
+  q = fmaf(z, q, 1.0f);
   float lnm = (2.0f * s) * q;
   float fe = (float)e;
-  return fe * LN2_HI + (fe * LN2_LO + lnm);
+  return fmaf(fe, LN2_HI, fmaf(fe, LN2_LO, lnm));
 }
 
 /* ---------------------------------------------------------------- Philox */
@@ -135,7 +136,9 @@ float orc_uniform(uint64_t seed, uint32_t stream_id, uint32_t t, int64_t p) {
  * d_c(0). The paper omits r_m; 41.03 deg is the value in the cited Watson
  * (2014) formula. */
 static const double AK_D = 0.9851, R2_D = 1.058, RE_D = 22.14, RM_D = 41.03, DC0_D = 14804.6;
-static const float AK_F = 0.9851f, R2_F = 1.058f, RE_F = 22.14f, RM_F = 41.03f;
+static const float AK_F = 0.9851f;
+/* reciprocals of the radii, each the float nearest 1 / (float radius) */
+static const float INV_R2_F = 1.0f / 1.058f, INV_RE_F = 1.0f / 22.14f, INV_RM_F = 1.0f / 41.03f;
 /* Eccentricities are clamped to this many degrees (beyond the visual field). */
 static const float E_MAX = 180.0f;
 
@@ -147,16 +150,26 @@ double orc_density64(double e) {
   return 2.0 * DC0_D * radial * (near + far);
 }
 
-float orc_density32(float e) {
-  /* d(e) / (2 d_c(0)), fixed order:
-   *   tm = 1 + e/r_m;  t2 = 1 + e/r_2;  A = a / (t2*t2);
-   *   B = (1 - a) * exp(-(e/r_e));  D = (A + B) / tm. */
-  float tm = 1.0f + e / RM_F;
-  float t2 = 1.0f + e / R2_F;
-  float A = AK_F / (t2 * t2);
+/* d(e) / (2 d_c(0)) of Eq. (cone_retinal_density) over one common denominator:
+ *   [a (1+e/r_2)^-2 + (1-a) exp(-e/r_e)] / (1+e/r_m)
+ *     = [a + (1-a) exp(-e/r_e) (1+e/r_2)^2] / [(1+e/r_2)^2 (1+e/r_m)]
+ * in the fixed order
+ *   t2 = fma(e, 1/r_2, 1);  q = t2*t2;  tm = fma(e, 1/r_m, 1);
+ *   B = (1-a) exp(-(e * (1/r_e)));  num = fma(B, q, a);  den = q*tm. */
+static void orc_density_parts(float e, float* num, float* den) {
+  float t2 = fmaf(e, INV_R2_F, 1.0f);
+  float q = t2 * t2;
+  float tm = fmaf(e, INV_RM_F, 1.0f);
   float one_minus_a = 1.0f - AK_F;
-  float B = one_minus_a * orc_exp(-(e / RE_F));
-  return (A + B) / tm;
+  float B = one_minus_a * orc_exp(-(e * INV_RE_F));
+  *num = fmaf(B, q, AK_F);
+  *den = q * tm;
+}
+
+float orc_density32(float e) {
+  float num, den;
+  orc_density_parts(e, &num, &den);
+  return num / den;
 }
 
 float orc_delta(const orc_config* cfg) {
@@ -177,7 +190,10 @@ float orc_weight32(const orc_config* cfg, int32_t x, int32_t y, float gx, float 
   if (e > E_MAX) e = E_MAX;
   float ef = cfg->r_f * delta;
   if (ef > E_MAX) ef = E_MAX;
-  float w = orc_density32(e) / orc_density32(ef);
+  /* d(e)/d(e_f) = num / (den * d(e_f)) with d(e_f) = num_f / den_f */
+  float num, den;
+  orc_density_parts(e, &num, &den);
+  float w = num / (den * orc_density32(ef));
   if (w > 1.0f) w = 1.0f;
   return w;
 }
@@ -207,13 +223,12 @@ void orc_pixel_step(int K, int bias, float w, float u, uint32_t t, const float r
   float k = E / w;
 
   /* Eq. (temporal-bias): R1.wsum <- R1.wsum * (1 - R2.wsum / (R1.wsum + R2.wsum)),
-   * with R2.wsum = w. The same factor scales every stored sample's weight,
-   * which the keys carry through the running product P. Skipped while the
-   * reservoir is empty (the factor would be 0 * (1 - w/w)). */
+   * with R2.wsum = w; the factor 1 - w/(W+w) is evaluated as W/(W+w). The same
+   * factor scales every stored sample's weight, which the keys carry through
+   * the running product P. Skipped while the reservoir is empty (the factor
+   * would be 0 * (1 - w/w)). */
   if (bias && *W > 0.0f) {
-    float den = *W + w;
-    float g = w / den;
-    float f = 1.0f - g;
+    float f = *W / (*W + w);
     *W = *W * f;
     *P = *P * f;
     if (*P < P_FLOOR) {

@@ -42,8 +42,8 @@ SIGNATURES = {
     "wrs_frame_index": (C.c_uint32, [_V]),
     "wrs_set_launch": (_I, [_V, _I, _I]),
     "wrs_get_launch": (_I, [_V, C.POINTER(_I), C.POINTER(_I)]),
-    "wrs_set_pipeline": (_I, [_V, _I, _I, _I]),
-    "wrs_get_pipeline": (_I, [_V, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "wrs_set_pipeline": (_I, [_V, _I, _I, _I, _I]),
+    "wrs_get_pipeline": (_I, [_V, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "wrs_set_wait_limit": (_I, [_V, C.c_uint64, C.c_uint32]),
     "wrs_check_status": (_I, [_V, _V]),
     "wrs_last_error": (C.c_char_p, []),

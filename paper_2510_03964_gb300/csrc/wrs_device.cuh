@@ -6,8 +6,9 @@
 //
 // Every floating-point step that decides which sample a slot holds is an
 // explicit round-to-nearest intrinsic (__fadd_rn, __fmul_rn, __fdiv_rn,
-// __fsqrt_rn), so the compiler cannot contract or reorder it: the stored keys,
-// indices, weights, W and P are a fixed function of the inputs, bit for bit.
+// __fsqrt_rn, __fmaf_rn), so the compiler cannot contract or reorder it: the
+// stored keys, indices, weights, W and P are a fixed function of the inputs,
+// bit for bit.
 // The resolve accumulates with explicit fused multiply-adds in slot order, so
 // the fused and standalone resolves agree bit for bit too.
 #pragma once
@@ -35,7 +36,9 @@ constexpr float kQ3 = 0x1.555556p-2f, kQ5 = 0x1.99999ap-3f, kQ7 = 0x1.24924ap-3f
                 kQ9 = 0x1.c71c72p-4f;
 // Watson's density parameters as printed with Eq. (cone_retinal_density); r_m,
 // absent from the paper, is the cited formula's 41.03 deg.
-constexpr float kA = 0.9851f, kR2 = 1.058f, kRe = 22.14f, kRm = 41.03f;
+constexpr float kA = 0.9851f;
+// floats nearest 1 / r_2, 1 / r_e, 1 / r_m (each radius first rounded to float)
+constexpr float kInvR2 = 0x1.e3ee96p-1f, kInvRe = 0x1.720250p-5f, kInvRm = 0x1.8f514ep-6f;
 constexpr float kEccMax = 180.0f;           // eccentricity clamp, degrees
 constexpr float kPFloor = 0x1p-64f;         // rescale the bias product below this
 constexpr float kPScale = 0x1p64f;
@@ -44,21 +47,22 @@ __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
 // exp(x) for x <= 0: x = n ln2 + r, |r| <= ln2/2; Taylor series of exp(r) to
 // degree 7 in Horner form; times 2^n through the exponent field.
 __device__ __forceinline__ float exp_nonpos(float x) {
   x = fminf(fmaxf(x, -87.0f), 0.0f);
   const float n = rintf(fmul(x, kLog2e));
-  const float r = fsub(fsub(x, fmul(n, kLn2Hi)), fmul(n, kLn2Lo));
-  float p = kF7;
-  p = fadd(kF6, fmul(r, p));
-  p = fadd(kF5, fmul(r, p));
-  p = fadd(kF4, fmul(r, p));
-  p = fadd(kF3, fmul(r, p));
-  p = fadd(0.5f, fmul(r, p));
-  p = fadd(1.0f, fmul(r, p));
-  p = fadd(1.0f, fmul(r, p));
+  float r = ffma(-n, kLn2Hi, x);
+  r = ffma(-n, kLn2Lo, r);
+  float p = ffma(r, kF7, kF6);
+  p = ffma(r, p, kF5);
+  p = ffma(r, p, kF4);
+  p = ffma(r, p, kF3);
+  p = ffma(r, p, 0.5f);
+  p = ffma(r, p, 1.0f);
+  p = ffma(r, p, 1.0f);
   const int ni = __float2int_rn(n);
   return fmul(p, __uint_as_float(static_cast<uint32_t>(ni + 127) << 23));
 }
@@ -75,14 +79,13 @@ __device__ __forceinline__ float log_pos(float u) {
   }
   const float s = fdiv(fsub(m, 1.0f), fadd(m, 1.0f));
   const float z = fmul(s, s);
-  float q = kQ9;
-  q = fadd(kQ7, fmul(z, q));
-  q = fadd(kQ5, fmul(z, q));
-  q = fadd(kQ3, fmul(z, q));
-  q = fadd(1.0f, fmul(z, q));
+  float q = ffma(z, kQ9, kQ7);
+  q = ffma(z, q, kQ5);
+  q = ffma(z, q, kQ3);
+  q = ffma(z, q, 1.0f);
   const float lnm = fmul(fmul(2.0f, s), q);
   const float fe = __int2float_rn(e);
-  return fadd(fmul(fe, kLn2Hi), fadd(fmul(fe, kLn2Lo), lnm));
+  return ffma(fe, kLn2Hi, ffma(fe, kLn2Lo, lnm));
 }
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds, key bumped by the Weyl
@@ -110,14 +113,22 @@ __device__ __forceinline__ float unit_uniform(uint32_t x) {
   return fmul(__uint2float_rn((x >> 8) | 1u), 0x1p-24f);
 }
 
-// d(e) / (2 d_c(0)) of Eq. (cone_retinal_density):
-//   ((a / (1+e/r_2)^2) + (1-a) exp(-e/r_e)) / (1 + e/r_m)
+// d(e) / (2 d_c(0)) of Eq. (cone_retinal_density) as num / den over one
+// denominator: num = a + (1-a) exp(-e/r_e) (1+e/r_2)^2,
+// den = (1+e/r_2)^2 (1+e/r_m).
+__device__ __forceinline__ void density_parts(float e, float& num, float& den) {
+  const float t2 = ffma(e, kInvR2, 1.0f);
+  const float q = fmul(t2, t2);
+  const float tm = ffma(e, kInvRm, 1.0f);
+  const float b_term = fmul(fsub(1.0f, kA), exp_nonpos(-fmul(e, kInvRe)));
+  num = ffma(b_term, q, kA);
+  den = fmul(q, tm);
+}
+
 __device__ __forceinline__ float density(float e) {
-  const float tm = fadd(1.0f, fdiv(e, kRm));
-  const float t2 = fadd(1.0f, fdiv(e, kR2));
-  const float a_term = fdiv(kA, fmul(t2, t2));
-  const float b_term = fmul(fsub(1.0f, kA), exp_nonpos(-fdiv(e, kRe)));
-  return fdiv(fadd(a_term, b_term), tm);
+  float num, den;
+  density_parts(e, num, den);
+  return fdiv(num, den);
 }
 
 // ---------------------------------------------------------------- parameters
@@ -159,7 +170,9 @@ __device__ __forceinline__ float pixel_weight(const StreamDev& s, float d_f, int
   const float d = __fsqrt_rn(fadd(fmul(dx, dx), fmul(dy, dy)));
   if (d <= s.r_f) return 1.0f;
   const float e = fminf(fmul(d, s.delta), kEccMax);
-  return fminf(fdiv(density(e), d_f), 1.0f);
+  float num, den;
+  density_parts(e, num, den);
+  return fminf(fdiv(num, fmul(den, d_f)), 1.0f);
 }
 
 // ---------------------------------------------------------------- vector I/O
@@ -227,9 +240,7 @@ __device__ __forceinline__ float bias_and_sum(int bias, float w, float k, float&
                                               bool& rescale) {
   rescale = false;
   if (bias && W > 0.0f) {
-    const float den = fadd(W, w);
-    const float g = fdiv(w, den);
-    const float fb = fsub(1.0f, g);
+    const float fb = fdiv(W, fadd(W, w));  // 1 - w / (W + w)
     W = fmul(W, fb);
     P = fmul(P, fb);
     if (P < kPFloor) {
@@ -261,6 +272,7 @@ struct Src {
   int64_t stride;
   int64_t at;
   const float* frame;
+  const float* u;  // the group's uniforms (u[0..PX-1]) if already drawn, else null
 };
 
 __device__ __forceinline__ Src global_src(const StreamDev& s, const FrameDev& f, int p0, bool vec) {
@@ -269,6 +281,7 @@ __device__ __forceinline__ Src global_src(const StreamDev& s, const FrameDev& f,
   r.stride = s.plane;
   r.at = p0;
   r.frame = nullptr;
+  r.u = nullptr;
   if (vec) {
     const int y = p0 / s.width;
     const int x = p0 - y * s.width;
@@ -331,7 +344,9 @@ __device__ __forceinline__ void store_rgb(float* dst, const float (&o)[N][3]) {
 // always go to the global planes. KT > 0 fixes K at compile time. VEC: the
 // group lies in one row and src.frame / f.out take vector accesses; otherwise
 // every pixel is addressed on its own (and may lie past the end of the image).
-template <int KT, bool F16, int PX, bool VEC>
+// FOV: a flush map is present (f.fov != null); without one the flush logic is
+// compiled out.
+template <int KT, bool F16, int PX, bool VEC, bool FOV>
 __device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f, int p0,
                                            const Src& src, float d_f) {
   const int K = KT > 0 ? KT : s.K;
@@ -379,14 +394,16 @@ __device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f
 
   bool flush[PX];
 #pragma unroll
-  for (int i = 0; i < PX; ++i)
-    flush[i] = (f.fov != nullptr) && valid[i] && f.fov[p0 + i] == 0xFFu;
+  for (int i = 0; i < PX; ++i) flush[i] = FOV && valid[i] && f.fov[p0 + i] == 0xFFu;
 
   // uniforms: one Philox block per 4 consecutive pixels, word p mod 4 (PX divides
   // 4 and p0 % PX == 0, so the group never straddles two blocks)
   static_assert(4 % PX == 0, "pixels per thread must divide 4");
   float u[PX];
-  {
+  if (src.u != nullptr) {
+#pragma unroll
+    for (int i = 0; i < PX; ++i) u[i] = src.u[i];
+  } else {
     const uint4 blk = philox4x32_10(
         make_uint4(static_cast<uint32_t>(p0) >> 2, f.t, s.stream_id, 0u), s.seed_lo, s.seed_hi);
 #pragma unroll

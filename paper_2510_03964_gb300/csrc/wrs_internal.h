@@ -18,6 +18,7 @@ struct wrs_ctx {
   int pipe;              // 1: use the pipelined kernel when the frame allows it
   int pipe_px;           // pipelined kernel: pixels per thread (tile = 256 * px)
   int pipe_stages;       // pipelined kernel: shared-memory stages
+  int pipe_ctas;         // pipelined kernel: CTAs per SM (0: as many as fit)
   uint64_t timeout_ns;   // bound on every device-side wait
   uint32_t test_extra_tx;  // > 0 only to exercise the timeout path in tests
 };
@@ -28,11 +29,11 @@ constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;  // 2 s
 constexpr size_t kSmemBudget = 227 * 1024 - 1024;       // dynamic shared memory per CTA we use
 
 uint32_t* wrs_status_word(const wrs_ctx* x);
-size_t wrs_pipe_stage_bytes(int K, bool f16, int px, bool resolve);
+size_t wrs_pipe_smem_bytes(int K, bool f16, int px, int stages, bool resolve);
 bool wrs_pipe_supported(const wrs_ctx* x, const float* frame, int64_t pitch, const float* out);
 cudaError_t wrs_launch_pipe(const wrs::StreamDev& s, const wrs::FrameDev& f, bool f16, int px,
-                            int stages, int sms, uint32_t* status, uint64_t timeout_ns,
-                            uint32_t extra_tx, cudaStream_t st);
+                            int stages, int sms, int ctas_per_sm, uint32_t* status,
+                            uint64_t timeout_ns, uint32_t extra_tx, cudaStream_t st);
 void wrs_default_pipe(int K, bool f16, int* px, int* stages);
 
 int wrs_fail(int code, const char* fmt, ...);

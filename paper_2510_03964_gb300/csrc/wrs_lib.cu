@@ -114,14 +114,11 @@ uint32_t* wrs_status_word(const wrs_ctx* x) {
 }
 
 void wrs_default_pipe(int K, bool f16, int* px, int* stages) {
-  // widest tile that still leaves room for two stages, then as many stages as fit (<= 4)
-  int p = 4;
-  while (p > 1 && 2 * wrs_pipe_stage_bytes(K, f16, p, true) + 64 > kSmemBudget) p /= 2;
-  size_t per = wrs_pipe_stage_bytes(K, f16, p, true);
-  int st = static_cast<int>(kSmemBudget / (per + 8));
-  if (st > 4) st = 4;
-  if (st < 1) st = 1;
-  *px = p;
+  // 256-pixel tiles, two stages (several CTAs per SM where they fit); three or
+  // four stages when one CTA's two stages would leave shared memory unused
+  *px = 1;
+  int st = 2;
+  while (st > 1 && wrs_pipe_smem_bytes(K, f16, 1, st, true) > kSmemBudget) --st;
   *stages = st;
 }
 
@@ -174,8 +171,11 @@ __global__ void __launch_bounds__(256, PX == 4 ? 2 : 3) push_kernel(const __grid
   const int64_t p0 = g * PX;
   if (p0 >= s.hw) return;
   const float d_f = wrs::fovea_density(s);
-  wrs::push_group<KT, F16, PX, VEC>(s, f, static_cast<int>(p0),
-                                    wrs::global_src(s, f, static_cast<int>(p0), VEC), d_f);
+  const wrs::Src src = wrs::global_src(s, f, static_cast<int>(p0), VEC);
+  if (f.fov != nullptr)
+    wrs::push_group<KT, F16, PX, VEC, true>(s, f, static_cast<int>(p0), src, d_f);
+  else
+    wrs::push_group<KT, F16, PX, VEC, false>(s, f, static_cast<int>(p0), src, d_f);
 }
 
 template <int KT, bool F16, int PX>
@@ -286,6 +286,7 @@ extern "C" int wrs_create(const wrs_config* cfg, void* d_state, size_t state_byt
   x->block = kDefaultBlock;
   x->px = kDefaultPx;
   x->pipe = 1;
+  x->pipe_ctas = 0;
   wrs_default_pipe(cfg->K, cfg->color_fp16 != 0, &x->pipe_px, &x->pipe_stages);
   x->timeout_ns = kDefaultTimeoutNs;
   x->test_extra_tx = 0;
@@ -344,7 +345,7 @@ extern "C" int wrs_push_frame(wrs_ctx* x, const float* d_frame, int64_t pitch, f
   cudaError_t e;
   if (x->pipe && wrs_pipe_supported(x, d_frame, pitch, d_out)) {
     e = wrs_launch_pipe(s, f, x->cfg.color_fp16 != 0, x->pipe_px, x->pipe_stages, x->sms,
-                        wrs_status_word(x), x->timeout_ns, x->test_extra_tx,
+                        x->pipe_ctas, wrs_status_word(x), x->timeout_ns, x->test_extra_tx,
                         static_cast<cudaStream_t>(stream));
   } else {
     const int px = wrs_effective_px(x, d_frame, pitch, d_out);
@@ -452,36 +453,42 @@ extern "C" int wrs_get_launch(const wrs_ctx* x, int* block_threads, int* px_per_
   return WRS_OK;
 }
 
-extern "C" int wrs_set_pipeline(wrs_ctx* x, int enable, int px_per_thread, int stages) {
+extern "C" int wrs_set_pipeline(wrs_ctx* x, int enable, int px_per_thread, int stages,
+                                int ctas_per_sm) {
   clear_error();
   if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
   int dpx, dst;
   wrs_default_pipe(x->cfg.K, x->cfg.color_fp16 != 0, &dpx, &dst);
+  const bool f16 = x->cfg.color_fp16 != 0;
   if (px_per_thread == 0) px_per_thread = dpx;
   if (px_per_thread != 1 && px_per_thread != 2 && px_per_thread != 4)
     return wrs_fail(WRS_ERR_ARG, "px_per_thread must be 1, 2 or 4");
   if (stages == 0) {
-    const size_t per = wrs_pipe_stage_bytes(x->cfg.K, x->cfg.color_fp16 != 0, px_per_thread, true);
-    stages = static_cast<int>(kSmemBudget / (per + 8));
-    if (stages > 4) stages = 4;
+    stages = 2;
+    while (stages > 1 && wrs_pipe_smem_bytes(x->cfg.K, f16, px_per_thread, stages, true) > kSmemBudget)
+      --stages;
   }
   if (stages < 1 || stages > 8) return wrs_fail(WRS_ERR_ARG, "stages must be in 1..8");
-  const size_t need = stages * (wrs_pipe_stage_bytes(x->cfg.K, x->cfg.color_fp16 != 0,
-                                                     px_per_thread, true) + 8);
+  if (ctas_per_sm < 0 || ctas_per_sm > 8) return wrs_fail(WRS_ERR_ARG, "ctas_per_sm must be in 0..8");
+  const size_t need = wrs_pipe_smem_bytes(x->cfg.K, f16, px_per_thread, stages, true);
   if (enable && need > kSmemBudget)
     return wrs_fail(WRS_ERR_ARG, "%d stages of %d px/thread need %zu B of shared memory (> %zu)",
                     stages, px_per_thread, need, kSmemBudget);
   x->pipe = enable ? 1 : 0;
   x->pipe_px = px_per_thread;
   x->pipe_stages = stages;
+  x->pipe_ctas = ctas_per_sm;
   return WRS_OK;
 }
 
-extern "C" int wrs_get_pipeline(const wrs_ctx* x, int* enable, int* px_per_thread, int* stages) {
-  if (!x || !enable || !px_per_thread || !stages) return wrs_fail(WRS_ERR_ARG, "NULL argument");
+extern "C" int wrs_get_pipeline(const wrs_ctx* x, int* enable, int* px_per_thread, int* stages,
+                                int* ctas_per_sm) {
+  if (!x || !enable || !px_per_thread || !stages || !ctas_per_sm)
+    return wrs_fail(WRS_ERR_ARG, "NULL argument");
   *enable = x->pipe;
   *px_per_thread = x->pipe_px;
   *stages = x->pipe_stages;
+  *ctas_per_sm = x->pipe_ctas;
   return WRS_OK;
 }
 

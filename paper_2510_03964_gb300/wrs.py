@@ -123,13 +123,16 @@ class Stream:
         check(load().wrs_get_launch(self._ctx, C.byref(b), C.byref(p)))
         return b.value, p.value
 
-    def set_pipeline(self, enable: bool = True, px_per_thread: int = 0, stages: int = 0):
-        check(load().wrs_set_pipeline(self._ctx, 1 if enable else 0, int(px_per_thread), int(stages)))
+    def set_pipeline(self, enable: bool = True, px_per_thread: int = 0, stages: int = 0,
+                     ctas_per_sm: int = 0):
+        check(load().wrs_set_pipeline(self._ctx, 1 if enable else 0, int(px_per_thread), int(stages),
+                                      int(ctas_per_sm)))
 
     def get_pipeline(self):
-        e, p, s = C.c_int(), C.c_int(), C.c_int()
-        check(load().wrs_get_pipeline(self._ctx, C.byref(e), C.byref(p), C.byref(s)))
-        return bool(e.value), p.value, s.value
+        """(enabled, pixels per thread, stages, CTAs per SM (0 = as many as fit))."""
+        e, p, s, c = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        check(load().wrs_get_pipeline(self._ctx, C.byref(e), C.byref(p), C.byref(s), C.byref(c)))
+        return bool(e.value), p.value, s.value, c.value
 
     def set_wait_limit(self, timeout_ns: int = 0, test_extra_tx: int = 0):
         check(load().wrs_set_wait_limit(self._ctx, int(timeout_ns), int(test_extra_tx)))

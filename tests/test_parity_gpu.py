@@ -55,16 +55,17 @@ def test_launch_shapes_agree(launch, K):
     run.compare()
 
 
-@pytest.mark.parametrize("pipeline", [(True, 1, 1), (True, 1, 4), (True, 2, 2), (True, 4, 2),
-                                      (True, 2, 3), (False, 0, 0)])
+@pytest.mark.parametrize("pipeline", [(True, 1, 1, 0), (True, 1, 4, 0), (True, 2, 2, 0), (True, 4, 2, 0),
+                                      (True, 2, 3, 0), (True, 1, 2, 1), (True, 1, 2, 3),
+                                      (False, 0, 0, 0)])
 @pytest.mark.parametrize("K,fp16", [(4, False), (8, False), (3, False), (8, True), (1, True)])
 def test_pipeline_shapes_agree(pipeline, K, fp16):
     """The pipelined kernel (tiles of 256*px pixels through `stages` shared-memory
     stages; 3840 pixels = a ragged last tile for every tile size) and the plain
     kernel give the same planes."""
-    enable, px, stages = pipeline
+    enable, px, stages, _ = pipeline
     cs = 2 if fp16 else 4
-    if enable and stages * 256 * px * (20 + 8 * K + 3 * K * cs) > 226 * 1024:
+    if enable and stages * 256 * px * (20 + 8 * K + 3 * K * cs) + 1024 * px + 64 > 226 * 1024:
         pytest.skip("these stages do not fit in shared memory (rejected by wrs_set_pipeline)")
     run = PairedRun(96, 40, K, r_f=10.0, frames=12, seed=5, jitter_px=20, color_fp16=fp16,
                     pipeline=pipeline)
@@ -78,13 +79,15 @@ def test_pipeline_rejects_oversized_stages():
     with pytest.raises(wrs.WrsError):
         st.set_pipeline(True, 4, 2)  # 2 x 184 KB
     st.set_pipeline(True, 2, 2)
-    assert st.get_pipeline() == (True, 2, 2)
+    assert st.get_pipeline() == (True, 2, 2, 0)
+    st.set_pipeline(True, 1, 3, 1)
+    assert st.get_pipeline() == (True, 1, 3, 1)
     st.close()
 
 
 def test_pipeline_many_tiles_per_cta():
     """More tiles than CTAs: every CTA walks several tiles through its stages."""
-    run = PairedRun(640, 480, 4, r_f=40.0, frames=6, seed=8, jitter_px=60, pipeline=(True, 2, 3),
+    run = PairedRun(640, 480, 4, r_f=40.0, frames=6, seed=8, jitter_px=60, pipeline=(True, 2, 3, 0),
                     pixels=np.arange(0, 640 * 480, 7))
     run.run()
     run.compare()
