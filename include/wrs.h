@@ -48,6 +48,7 @@ extern "C" {
 #define WRS_ERR_STATE 5    /* context in the wrong state (e.g. counter exhausted) */
 
 #define WRS_MAX_K 16
+#define WRS_MAX_BATCH 64  /* streams in one wrs_push_batch launch */
 #define WRS_EMPTY_SLOT 0xFFFFFFFFu /* sample index of an unoccupied slot */
 
 typedef struct wrs_ctx wrs_ctx;
@@ -180,6 +181,40 @@ int wrs_set_wait_limit(wrs_ctx* ctx, uint64_t timeout_ns, uint32_t test_extra_tx
  * WRS_ERR_TIMEOUT if a wait gave up since the last check (the frames pushed
  * meanwhile may be partly applied). */
 int wrs_check_status(wrs_ctx* ctx, wrs_stream_t stream);
+
+/* ------------------------------------------------------------------ batches */
+
+/* A batch launcher: pushes one frame into each of up to max_streams streams
+ * (any mix of sizes, K and colour precision, all on one device) with a single
+ * persistent launch. The launch is a kernel node of a CUDA graph, built on
+ * the first push and updated in place for every later push. The library owns
+ * the launcher and its graphs (host objects and driver handles only: no
+ * device memory). */
+typedef struct wrs_batch wrs_batch;
+int wrs_batch_create(int max_streams, wrs_batch** out);
+int wrs_batch_destroy(wrs_batch* batch);
+
+/* Tile and launch shape: tiles of 256 * px_per_thread pixels (1, 2 or 4),
+ * `stages` shared-memory stages (0: two, or one if two do not fit),
+ * ctas_per_sm persistent CTAs per SM (0: as many as fit), use_graph = 0 for a
+ * plain launch instead of the graph. Chosen by the autotuner. */
+int wrs_batch_set_launch(wrs_batch* batch, int px_per_thread, int stages, int ctas_per_sm,
+                         int use_graph);
+int wrs_batch_get_launch(const wrs_batch* batch, int* px_per_thread, int* stages,
+                         int* ctas_per_sm, int* use_graph);
+
+/* Pushes d_frames[i] with gaze (gaze_xy[2i], gaze_xy[2i+1]) into ctxs[i] for
+ * i < n, the same per-pixel steps as wrs_push_frame (Sec. 4), with optional
+ * flush maps (d_fov_maps NULL or per-stream NULL) and fused resolves into
+ * d_outs[i] (d_outs NULL or per-stream NULL). Every frame must be unpadded
+ * (pitch 3 * width), width % 4 == 0, frame and out 16-byte aligned; a stream
+ * may appear once per batch. gaze_xy is host memory. Each stream's state and
+ * output are bit-identical to pushing it alone. Every stream's frame counter
+ * advances. Errors: WRS_ERR_ARG, WRS_ERR_STATE, WRS_ERR_CUDA (nothing is
+ * launched on error). */
+int wrs_push_batch(wrs_batch* batch, int n, wrs_ctx* const* ctxs, const float* const* d_frames,
+                   const float* gaze_xy, const uint8_t* const* d_fov_maps, float* const* d_outs,
+                   wrs_stream_t stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* wrs_last_error(void);

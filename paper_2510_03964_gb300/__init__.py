@@ -8,9 +8,9 @@ the library does all of the work, and nothing falls back to the CPU: without
 the built library every call raises.
 """
 from ._lib import WrsError, header_functions, load
-from .wrs import Stream, make_config, state_bytes, state_layout, unpack_state
+from .wrs import Batch, Stream, make_config, state_bytes, state_layout, unpack_state
 
-__all__ = ["Stream", "make_config", "state_bytes", "state_layout", "unpack_state", "WrsError",
+__all__ = ["Batch", "Stream", "make_config", "state_bytes", "state_layout", "unpack_state", "WrsError",
            "load", "header_functions"]
 
 

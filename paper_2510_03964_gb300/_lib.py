@@ -10,6 +10,7 @@ from . import build as _build
 
 WRS_OK, WRS_ERR_ARG, WRS_ERR_CUDA, WRS_ERR_BUDGET, WRS_ERR_TIMEOUT, WRS_ERR_STATE = range(6)
 WRS_MAX_K = 16
+WRS_MAX_BATCH = 64
 WRS_EMPTY_SLOT = 0xFFFFFFFF
 HEADER = os.path.join(_build.INCLUDE, "wrs.h")
 
@@ -46,6 +47,11 @@ SIGNATURES = {
     "wrs_get_pipeline": (_I, [_V, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "wrs_set_wait_limit": (_I, [_V, C.c_uint64, C.c_uint32]),
     "wrs_check_status": (_I, [_V, _V]),
+    "wrs_batch_create": (_I, [_I, C.POINTER(_V)]),
+    "wrs_batch_destroy": (_I, [_V]),
+    "wrs_batch_set_launch": (_I, [_V, _I, _I, _I, _I]),
+    "wrs_batch_get_launch": (_I, [_V, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "wrs_push_batch": (_I, [_V, _I, _V, _V, _V, _V, _V, _V]),
     "wrs_last_error": (C.c_char_p, []),
 }
 

@@ -57,7 +57,7 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Waits for phase `parity` of `bar` to complete; false once limit_ns has passed.
-__device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+static __device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {

@@ -1,0 +1,352 @@
+// Batched form: many streams of uneven resolution, K and colour precision in
+// one persistent launch, captured once in a CUDA graph.
+//
+// The launch's descriptor (every stream's planes, frame, gaze, frame index and
+// first tile) travels by value as the kernel parameter, so a batch needs no
+// device memory of its own. Tiles of T = 256 * PX pixels of all streams are
+// numbered stream after stream and dealt to the persistent CTAs round-robin,
+// which spreads every stream (and so every K) evenly over the CTAs. Each tile
+// goes through the same bulk-copy / uniform / compute pipeline as the
+// single-stream kernel (wrs_async.cuh), with the arithmetic chosen per tile by
+// the stream's K and colour precision; results are bit-identical to pushing
+// each stream on its own.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "wrs.h"
+#include "wrs_async.cuh"
+#include "wrs_device.cuh"
+#include "wrs_internal.h"
+
+using wrs::FrameDev;
+using wrs::StageLayout;
+using wrs::StreamDev;
+
+namespace {
+
+constexpr int kMaxBatch = WRS_MAX_BATCH;
+
+struct BatchEntry {
+  StreamDev s;
+  FrameDev f;
+  uint32_t* status;
+  int tile0;   // first global tile of this stream
+  int code;    // arithmetic variant: 0 K=4 f16, 1 K=8 f16, 2 K=4 f32, 3 K=8 f32, 4 any K f16, 5 any K f32
+};
+
+struct BatchArgs {
+  int n;
+  int ntiles;
+  int stages;
+  uint32_t stage_bytes;  // largest stage of any stream in the batch
+  uint64_t timeout_ns;
+  BatchEntry e[kMaxBatch];
+};
+// kernel parameters may take up to 32764 bytes on sm_70 and later (CUDA 12.1+)
+static_assert(sizeof(BatchArgs) <= 32000, "batch descriptor too large for a kernel parameter");
+
+__device__ __forceinline__ int entry_of(const BatchArgs& a, int g) {
+  int lo = 0, hi = a.n - 1;  // last entry with tile0 <= g
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.e[mid].tile0 <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool entry_f16(const BatchEntry& e) {
+  return e.code == 0 || e.code == 1 || e.code == 4;
+}
+
+template <int PX>
+__device__ __forceinline__ void batch_issue(const BatchArgs& a, uint8_t* smem, uint64_t* bars,
+                                            int it, int g, int lane) {
+  constexpr int T = 256 * PX;
+  const BatchEntry& e = a.e[entry_of(a, g)];
+  const int cs = entry_f16(e) ? 2 : 4;
+  const bool resolve = e.f.out != nullptr;
+  const StageLayout L = wrs::stage_layout(T, e.s.K, cs, resolve);
+  const int stg = it % a.stages;
+  wrs::issue_tile_copies<T>(e.s, e.f, e.s.K, cs, resolve, L, smem + stg * a.stage_bytes,
+                            &bars[stg], static_cast<int64_t>(g - e.tile0) * T, 0u, lane);
+}
+
+template <int PX>
+__global__ void __launch_bounds__(256, PX == 1 ? 2 : 1)
+    batch_kernel(const __grid_constant__ BatchArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  constexpr int T = 256 * PX;
+  const int S = a.stages;
+  float* ubuf = reinterpret_cast<float*>(smem + S * a.stage_bytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * a.stage_bytes + 4 * T);
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) wrs::mbar_init(&bars[i], 1);
+    wrs::fence_mbar_init();
+  }
+  __syncthreads();
+
+  const int first = blockIdx.x, step = gridDim.x;
+  const int my_tiles = first < a.ntiles ? (a.ntiles - 1 - first) / step + 1 : 0;
+  const int prologue = min(S - 1, my_tiles);
+  if (tid < 32)
+    for (int it = 0; it < prologue; ++it) batch_issue<PX>(a, smem, bars, it, first + it * step, lane);
+
+  int it = 0;
+  bool ok = true;
+  int failed_entry = 0;
+  for (; it < my_tiles; ++it) {
+    const int nxt = it + S - 1;
+    if (tid < 32 && nxt < my_tiles) batch_issue<PX>(a, smem, bars, nxt, first + nxt * step, lane);
+    const int g = first + it * step;
+    const int ei = entry_of(a, g);
+    const BatchEntry& e = a.e[ei];
+    const int64_t p0 = static_cast<int64_t>(g - e.tile0) * T;
+    wrs::draw_tile_uniforms<T>(e.s, e.f, p0, ubuf, tid);
+    const int stg = it % S;
+    const bool landed = wrs::mbar_wait_bounded(&bars[stg], (it / S) & 1u, a.timeout_ns);
+    if (!__syncthreads_and(landed)) {
+      ok = false;
+      failed_entry = ei;
+      break;
+    }
+    const bool resolve = e.f.out != nullptr;
+    const uint8_t* st = smem + stg * a.stage_bytes;
+    const float d_f = wrs::fovea_density(e.s);
+    switch (e.code) {
+      case 0: wrs::compute_tile<4, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 2, resolve), st, ubuf, p0, d_f, tid); break;
+      case 1: wrs::compute_tile<8, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 2, resolve), st, ubuf, p0, d_f, tid); break;
+      case 2: wrs::compute_tile<4, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 4, resolve), st, ubuf, p0, d_f, tid); break;
+      case 3: wrs::compute_tile<8, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 4, resolve), st, ubuf, p0, d_f, tid); break;
+      case 4: wrs::compute_tile<0, true, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 2, resolve), st, ubuf, p0, d_f, tid); break;
+      default: wrs::compute_tile<0, false, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 4, resolve), st, ubuf, p0, d_f, tid); break;
+    }
+    __syncthreads();
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(a.e[failed_entry].status, static_cast<uint32_t>(WRS_ERR_TIMEOUT));
+    const int last = min(it + S, my_tiles);
+    for (int j = it; j < last; ++j)
+      wrs::mbar_wait_bounded(&bars[j % S], (j / S) & 1u, a.timeout_ns);
+  }
+}
+
+template <int PX>
+const void* batch_fn() {
+  return reinterpret_cast<const void*>(&batch_kernel<PX>);
+}
+
+const void* batch_kernel_for(int px) {
+  switch (px) {
+    case 4: return batch_fn<4>();
+    case 2: return batch_fn<2>();
+    default: return batch_fn<1>();
+  }
+}
+
+}  // namespace
+
+struct wrs_batch {
+  int max_streams;
+  int px, stages, ctas_per_sm, use_graph;
+  BatchArgs* args;            // host copy of the launch descriptor
+  // one captured graph per pixels-per-thread choice
+  cudaGraph_t graph[3];
+  cudaGraphExec_t exec[3];
+  cudaGraphNode_t node[3];
+  size_t configured_smem[3];
+  int device;
+};
+
+static int px_slot(int px) { return px == 4 ? 2 : (px == 2 ? 1 : 0); }
+
+extern "C" int wrs_batch_create(int max_streams, wrs_batch** out) {
+  if (!out) return wrs_fail(WRS_ERR_ARG, "output pointer is NULL");
+  *out = nullptr;
+  if (max_streams < 1 || max_streams > kMaxBatch)
+    return wrs_fail(WRS_ERR_ARG, "max_streams must be in 1..%d", kMaxBatch);
+  wrs_batch* b = new (std::nothrow) wrs_batch;
+  if (!b) return wrs_fail(WRS_ERR_ARG, "out of host memory");
+  std::memset(b, 0, sizeof *b);
+  b->args = new (std::nothrow) BatchArgs;
+  if (!b->args) {
+    delete b;
+    return wrs_fail(WRS_ERR_ARG, "out of host memory");
+  }
+  std::memset(b->args, 0, sizeof(BatchArgs));
+  b->max_streams = max_streams;
+  b->px = 1;
+  b->stages = 0;
+  b->ctas_per_sm = 0;
+  b->use_graph = 1;
+  b->device = -1;
+  *out = b;
+  return WRS_OK;
+}
+
+extern "C" int wrs_batch_destroy(wrs_batch* b) {
+  if (!b) return WRS_OK;
+  for (int i = 0; i < 3; ++i) {
+    if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
+    if (b->graph[i]) cudaGraphDestroy(b->graph[i]);
+  }
+  delete b->args;
+  delete b;
+  return WRS_OK;
+}
+
+extern "C" int wrs_batch_set_launch(wrs_batch* b, int px_per_thread, int stages, int ctas_per_sm,
+                                    int use_graph) {
+  if (!b) return wrs_fail(WRS_ERR_ARG, "batch is NULL");
+  if (px_per_thread == 0) px_per_thread = 1;
+  if (px_per_thread != 1 && px_per_thread != 2 && px_per_thread != 4)
+    return wrs_fail(WRS_ERR_ARG, "px_per_thread must be 1, 2 or 4");
+  if (stages < 0 || stages > 8) return wrs_fail(WRS_ERR_ARG, "stages must be in 0..8");
+  if (ctas_per_sm < 0 || ctas_per_sm > 8) return wrs_fail(WRS_ERR_ARG, "ctas_per_sm must be in 0..8");
+  b->px = px_per_thread;
+  b->stages = stages;
+  b->ctas_per_sm = ctas_per_sm;
+  b->use_graph = use_graph ? 1 : 0;
+  return WRS_OK;
+}
+
+extern "C" int wrs_batch_get_launch(const wrs_batch* b, int* px_per_thread, int* stages,
+                                    int* ctas_per_sm, int* use_graph) {
+  if (!b || !px_per_thread || !stages || !ctas_per_sm || !use_graph)
+    return wrs_fail(WRS_ERR_ARG, "NULL argument");
+  *px_per_thread = b->px;
+  *stages = b->stages;
+  *ctas_per_sm = b->ctas_per_sm;
+  *use_graph = b->use_graph;
+  return WRS_OK;
+}
+
+static int code_of(const wrs_config& c) {
+  const bool f16 = c.color_fp16 != 0;
+  if (c.K == 4) return f16 ? 0 : 2;
+  if (c.K == 8) return f16 ? 1 : 3;
+  return f16 ? 4 : 5;
+}
+
+extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
+                              const float* const* d_frames, const float* gaze_xy,
+                              const uint8_t* const* d_fov_maps, float* const* d_outs,
+                              wrs_stream_t stream) {
+  if (!b || !ctxs || !d_frames || !gaze_xy) return wrs_fail(WRS_ERR_ARG, "NULL argument");
+  if (n < 1 || n > b->max_streams)
+    return wrs_fail(WRS_ERR_ARG, "n must be in 1..%d (got %d)", b->max_streams, n);
+  BatchArgs& a = *b->args;
+  const int T = 256 * b->px;
+  int64_t tiles = 0;
+  uint32_t stage_bytes = 0;
+  int device = -1;
+  for (int i = 0; i < n; ++i) {
+    wrs_ctx* x = ctxs[i];
+    if (!x) return wrs_fail(WRS_ERR_ARG, "ctxs[%d] is NULL", i);
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == x) return wrs_fail(WRS_ERR_ARG, "stream %d appears twice in the batch", i);
+    if (device < 0) device = x->device;
+    if (x->device != device) return wrs_fail(WRS_ERR_ARG, "all streams of a batch must share a device");
+    const float* fr = d_frames[i];
+    float* out = d_outs ? d_outs[i] : nullptr;
+    if (!fr || !wrs_pipe_supported(x, fr, 3 * static_cast<int64_t>(x->cfg.width), out))
+      return wrs_fail(WRS_ERR_ARG,
+                      "stream %d: batched frames need width %% 4 == 0 and 16-byte aligned, "
+                      "unpadded frame and out",
+                      i);
+    const float gx = gaze_xy[2 * i], gy = gaze_xy[2 * i + 1];
+    if (!std::isfinite(gx) || !std::isfinite(gy))
+      return wrs_fail(WRS_ERR_ARG, "stream %d: gaze must be finite", i);
+    if (x->t == 0xFFFFFFFFu) return wrs_fail(WRS_ERR_STATE, "stream %d: frame counter exhausted", i);
+    BatchEntry& e = a.e[i];
+    e.s = wrs_stream_dev(x);
+    e.f.frame = fr;
+    e.f.pitch = 3 * static_cast<int64_t>(x->cfg.width);
+    e.f.fov = d_fov_maps ? d_fov_maps[i] : nullptr;
+    e.f.out = out;
+    e.f.gx = gx;
+    e.f.gy = gy;
+    e.f.t = x->t;
+    e.status = wrs_status_word(x);
+    e.tile0 = static_cast<int>(tiles);
+    e.code = code_of(x->cfg);
+    tiles += (static_cast<int64_t>(e.s.hw) + T - 1) / T;
+    const size_t sb = wrs_pipe_smem_bytes(x->cfg.K, x->cfg.color_fp16 != 0, b->px, 1, out != nullptr) -
+                      4u * T - 8u;  // one stage
+    if (sb > stage_bytes) stage_bytes = static_cast<uint32_t>(sb);
+  }
+  if (tiles > 0x7FFFFFFF) return wrs_fail(WRS_ERR_ARG, "batch too large");
+  int stages = b->stages;
+  if (stages == 0) {
+    stages = 2;
+    while (stages > 1 && static_cast<size_t>(stages) * stage_bytes + 4u * T + 8u * stages > kSmemBudget)
+      --stages;
+  }
+  const size_t smem = static_cast<size_t>(stages) * stage_bytes + 4u * T + 8u * stages;
+  if (smem > kSmemBudget)
+    return wrs_fail(WRS_ERR_ARG, "%d stages of %u B exceed shared memory", stages, stage_bytes);
+  a.n = n;
+  a.ntiles = static_cast<int>(tiles);
+  a.stages = stages;
+  a.stage_bytes = stage_bytes;
+  a.timeout_ns = ctxs[0]->timeout_ns;
+
+  const int slot = px_slot(b->px);
+  const void* fn = batch_kernel_for(b->px);
+  cudaError_t e = cudaSuccess;
+  if (b->device != device) {
+    // a new device: drop graphs and attribute settings made for another one
+    for (int i = 0; i < 3; ++i) {
+      if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
+      if (b->graph[i]) cudaGraphDestroy(b->graph[i]);
+      b->exec[i] = nullptr;
+      b->graph[i] = nullptr;
+      b->configured_smem[i] = 0;
+    }
+    b->device = device;
+  }
+  if (smem > b->configured_smem[slot]) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_batch: shared memory attribute");
+    b->configured_smem[slot] = smem;
+  }
+  int fit = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, 256, smem);
+  if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_batch: occupancy");
+  if (fit < 1) return wrs_fail(WRS_ERR_ARG, "batch kernel does not fit on an SM");
+  const int per_sm = b->ctas_per_sm > 0 && b->ctas_per_sm < fit ? b->ctas_per_sm : fit;
+  const int64_t want = static_cast<int64_t>(ctxs[0]->sms) * per_sm;
+  const int grid = static_cast<int>(tiles < want ? tiles : want);
+
+  cudaKernelNodeParams kp;
+  std::memset(&kp, 0, sizeof kp);
+  void* params[1] = {&a};
+  kp.func = const_cast<void*>(fn);
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(256);
+  kp.sharedMemBytes = static_cast<unsigned>(smem);
+  kp.kernelParams = params;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (b->use_graph) {
+    if (!b->exec[slot]) {
+      e = cudaGraphCreate(&b->graph[slot], 0);
+      if (e == cudaSuccess) e = cudaGraphAddKernelNode(&b->node[slot], b->graph[slot], nullptr, 0, &kp);
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[slot], b->graph[slot], 0);
+      if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_batch: graph build");
+    } else {
+      e = cudaGraphExecKernelNodeSetParams(b->exec[slot], b->node[slot], &kp);
+      if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_batch: graph update");
+    }
+    e = cudaGraphLaunch(b->exec[slot], st);
+    if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_batch: graph launch");
+  } else {
+    e = cudaLaunchKernel(fn, kp.gridDim, kp.blockDim, params, smem, st);
+    if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_batch: launch");
+  }
+  for (int i = 0; i < n; ++i) ctxs[i]->t += 1;
+  return WRS_OK;
+}

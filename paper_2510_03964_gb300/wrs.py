@@ -189,3 +189,50 @@ def unpack_state(buf: np.ndarray, lay: WrsLayout, K: int, hw: int, color_fp16: b
 
 __all__ = ["Stream", "make_config", "state_bytes", "state_layout", "unpack_state", "WrsError",
            "WRS_EMPTY_SLOT"]
+
+
+class Batch:
+    """One persistent launch (a CUDA-graph kernel node) that pushes a frame into
+    each of up to ``max_streams`` streams of any size, K and colour precision."""
+
+    def __init__(self, max_streams: int = 64):
+        b = C.c_void_p()
+        check(load().wrs_batch_create(int(max_streams), C.byref(b)))
+        self._b = b
+        self.max_streams = int(max_streams)
+
+    def set_launch(self, px_per_thread: int = 1, stages: int = 0, ctas_per_sm: int = 0,
+                   use_graph: bool = True):
+        check(load().wrs_batch_set_launch(self._b, int(px_per_thread), int(stages), int(ctas_per_sm),
+                                          1 if use_graph else 0))
+
+    def get_launch(self):
+        p, s, c, g = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        check(load().wrs_batch_get_launch(self._b, C.byref(p), C.byref(s), C.byref(c), C.byref(g)))
+        return p.value, s.value, c.value, bool(g.value)
+
+    def push(self, streams, frames, gazes, fov_maps=None, outs=None, stream=None):
+        n = len(streams)
+        if not (len(frames) == n and len(gazes) == n):
+            raise ValueError("streams, frames and gazes must have the same length")
+        ctxs = (C.c_void_p * n)(*[s._ctx.value for s in streams])
+        fr = (C.c_void_p * n)(*[_dev_ptr(f, torch.float32, "frame") for f in frames])
+        gz = (C.c_float * (2 * n))(*[float(v) for g in gazes for v in (g[0], g[1])])
+        fm = None if fov_maps is None else (C.c_void_p * n)(
+            *[_dev_ptr(m, torch.uint8, "fov_map") for m in fov_maps])
+        ot = None if outs is None else (C.c_void_p * n)(*[_dev_ptr(o, torch.float32, "out") for o in outs])
+        for f, s in zip(frames, streams):
+            if tuple(f.shape[-3:]) != (s.height, s.width, 3) or not f.is_contiguous():
+                raise ValueError("frames must be contiguous [H][W][3] float32 tensors")
+        check(load().wrs_push_batch(self._b, n, ctxs, fr, gz, fm, ot, _stream_handle(stream)))
+
+    def close(self):
+        if self._b:
+            load().wrs_batch_destroy(self._b)
+            self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
