@@ -28,6 +28,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // global -> shared bulk copy of `bytes` (multiple of 16, both addresses 16-byte
 // aligned), completing `bytes` transactions on `bar`
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
@@ -126,24 +130,24 @@ __device__ __forceinline__ void issue_tile_copies(const StreamDev& s, const Fram
   }
 }
 
-// The tile's uniforms: one Philox block per 4 pixels, written to u[0 .. T-1].
-// Threads tid < T/4 each draw one block.
+// The tile's uniforms, drawn by one warp: one Philox block per 4 pixels,
+// written to u[0 .. T-1].
 template <int T>
-__device__ __forceinline__ void draw_tile_uniforms(const StreamDev& s, const FrameDev& f,
-                                                   int64_t p0, float* u, int tid) {
-  if (tid < T / 4) {
-    const uint32_t q = static_cast<uint32_t>((p0 >> 2) + tid);
-    const uint4 b = philox4x32_10(make_uint4(q, f.t, s.stream_id, 0u), s.seed_lo, s.seed_hi);
+__device__ __forceinline__ void draw_tile_uniforms_warp(const StreamDev& s, const FrameDev& f,
+                                                        int64_t p0, float* u, int lane) {
+  for (int q = lane; q < T / 4; q += 32) {
+    const uint32_t blk = static_cast<uint32_t>((p0 >> 2) + q);
+    const uint4 b = philox4x32_10(make_uint4(blk, f.t, s.stream_id, 0u), s.seed_lo, s.seed_hi);
     float4 v;
     v.x = unit_uniform(b.x);
     v.y = unit_uniform(b.y);
     v.z = unit_uniform(b.z);
     v.w = unit_uniform(b.w);
-    reinterpret_cast<float4*>(u)[tid] = v;
+    reinterpret_cast<float4*>(u)[q] = v;
   }
 }
 
-// Computes the thread's PX pixels of a landed tile from shared memory.
+// Computes consumer thread `tid`'s PX pixels of a landed tile from shared memory.
 template <int KT, bool F16, int PX, int T>
 __device__ __forceinline__ void compute_tile(const StreamDev& s, const FrameDev& f,
                                              const StageLayout& L, const uint8_t* st,
@@ -165,6 +169,105 @@ __device__ __forceinline__ void compute_tile(const StreamDev& s, const FrameDev&
     push_group<KT, F16, PX, true, true>(s, f, static_cast<int>(p), src, d_f);
   else
     push_group<KT, F16, PX, true, false>(s, f, static_cast<int>(p), src, d_f);
+}
+
+// ---------------------------------------------------------------- warp-specialised loop
+
+// Shared-memory ring of S stages, each holding one tile's planes followed by
+// its uniforms, then the S "full" and S "empty" barriers and a flag word.
+struct Ring {
+  uint8_t* base;
+  uint32_t stage_bytes;  // planes of the largest tile layout used
+  uint32_t stride;       // stage_bytes + 4 * T
+  int S;
+  uint64_t* full;
+  uint64_t* empty;
+  int* flag;             // non-zero once some wait gave up
+
+  __device__ uint8_t* stage(int i) const { return base + i * stride; }
+  __device__ float* u(int i) const { return reinterpret_cast<float*>(base + i * stride + stage_bytes); }
+};
+
+__host__ __device__ __forceinline__ size_t ring_bytes(uint32_t stage_bytes, int T, int S) {
+  return static_cast<size_t>(S) * (stage_bytes + 4u * T) + 16u * S + 16u;
+}
+
+__device__ __forceinline__ Ring make_ring(uint8_t* smem, uint32_t stage_bytes, int T, int S) {
+  Ring r;
+  r.base = smem;
+  r.stage_bytes = stage_bytes;
+  r.stride = stage_bytes + 4u * T;
+  r.S = S;
+  r.full = reinterpret_cast<uint64_t*>(smem + static_cast<size_t>(S) * r.stride);
+  r.empty = r.full + S;
+  r.flag = reinterpret_cast<int*>(r.empty + S);
+  return r;
+}
+
+// Thread 0 initialises the barriers (full: one arrival, the producer's;
+// empty: one arrival per consumer warp) and the flag; the caller then
+// synchronises the block.
+__device__ __forceinline__ void init_ring(const Ring& r, int consumer_warps) {
+  for (int i = 0; i < r.S; ++i) {
+    mbar_init(&r.full[i], 1);
+    mbar_init(&r.empty[i], consumer_warps);
+  }
+  *r.flag = 0;
+  fence_mbar_init();
+}
+
+__device__ __forceinline__ void raise_flag(const Ring& r) {
+  atomicExch(r.flag, 1);
+}
+
+__device__ __forceinline__ bool flag_raised(const Ring& r) {
+  return *reinterpret_cast<volatile int*>(r.flag) != 0;
+}
+
+// Producer warp: for each of its tiles, waits until the stage is free, draws
+// the tile's uniforms into the stage, arms the stage's full barrier and
+// issues the tile's copies. `tile_fn(it, stage, u, full_bar, lane)` does the
+// drawing and the copies for iteration it. Returns the number of tiles issued.
+template <typename TileFn>
+__device__ __forceinline__ int produce(const Ring& r, int my_tiles, uint64_t timeout_ns, int lane,
+                                       TileFn tile_fn) {
+  int it = 0;
+  for (; it < my_tiles; ++it) {
+    const int stg = it % r.S;
+    if (it >= r.S && !mbar_wait_bounded(&r.empty[stg], ((it / r.S) - 1) & 1u, timeout_ns)) {
+      raise_flag(r);
+      break;
+    }
+    if (flag_raised(r)) break;
+    tile_fn(it, r.stage(stg), r.u(stg), &r.full[stg], lane);
+  }
+  return it;
+}
+
+// Consumer warp: for each tile, waits for its stage to land, computes it
+// (`compute_fn(it, stage, u)`), and releases the stage.
+template <typename ComputeFn>
+__device__ __forceinline__ void consume(const Ring& r, int my_tiles, uint64_t timeout_ns, int lane,
+                                        ComputeFn compute_fn) {
+  for (int it = 0; it < my_tiles; ++it) {
+    const int stg = it % r.S;
+    if (!mbar_wait_bounded(&r.full[stg], (it / r.S) & 1u, timeout_ns)) {
+      raise_flag(r);
+      break;
+    }
+    compute_fn(it, r.stage(stg), r.u(stg));
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&r.empty[stg]);
+  }
+}
+
+// After the loops (and a block barrier): if a wait gave up, the producer warp
+// waits (bounded) for the copies of the last S tiles it issued, so that none
+// lands in shared memory after the CTA has exited.
+__device__ __forceinline__ void drain(const Ring& r, int issued, uint64_t timeout_ns) {
+  const int from = issued > r.S ? issued - r.S : 0;
+  for (int j = from; j < issued; ++j)
+    mbar_wait_bounded(&r.full[j % r.S], (j / r.S) & 1u, timeout_ns);
 }
 
 }  // namespace wrs

@@ -61,77 +61,62 @@ __device__ __forceinline__ bool entry_f16(const BatchEntry& e) {
   return e.code == 0 || e.code == 1 || e.code == 4;
 }
 
-template <int PX>
-__device__ __forceinline__ void batch_issue(const BatchArgs& a, uint8_t* smem, uint64_t* bars,
-                                            int it, int g, int lane) {
-  constexpr int T = 256 * PX;
-  const BatchEntry& e = a.e[entry_of(a, g)];
-  const int cs = entry_f16(e) ? 2 : 4;
-  const bool resolve = e.f.out != nullptr;
-  const StageLayout L = wrs::stage_layout(T, e.s.K, cs, resolve);
-  const int stg = it % a.stages;
-  wrs::issue_tile_copies<T>(e.s, e.f, e.s.K, cs, resolve, L, smem + stg * a.stage_bytes,
-                            &bars[stg], static_cast<int64_t>(g - e.tile0) * T, 0u, lane);
-}
+constexpr int kConsumerWarps = 8;
+constexpr int kBatchThreads = (kConsumerWarps + 1) * 32;
 
+// Warp-specialised like the single-stream pipelined kernel: warp 8 draws each
+// tile's uniforms and issues its copies, warps 0..7 compute it.
 template <int PX>
-__global__ void __launch_bounds__(256, PX == 1 ? 2 : 1)
+__global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
     batch_kernel(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
-  constexpr int T = 256 * PX;
-  const int S = a.stages;
-  float* ubuf = reinterpret_cast<float*>(smem + S * a.stage_bytes);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * a.stage_bytes + 4 * T);
+  constexpr int T = kConsumerWarps * 32 * PX;
+  const wrs::Ring r = wrs::make_ring(smem, a.stage_bytes, T, a.stages);
   const int tid = threadIdx.x;
+  const int warp = tid >> 5;
   const int lane = tid & 31;
-  if (tid == 0) {
-    for (int i = 0; i < S; ++i) wrs::mbar_init(&bars[i], 1);
-    wrs::fence_mbar_init();
-  }
+  if (tid == 0) wrs::init_ring(r, kConsumerWarps);
   __syncthreads();
 
   const int first = blockIdx.x, step = gridDim.x;
   const int my_tiles = first < a.ntiles ? (a.ntiles - 1 - first) / step + 1 : 0;
-  const int prologue = min(S - 1, my_tiles);
-  if (tid < 32)
-    for (int it = 0; it < prologue; ++it) batch_issue<PX>(a, smem, bars, it, first + it * step, lane);
-
-  int it = 0;
-  bool ok = true;
-  int failed_entry = 0;
-  for (; it < my_tiles; ++it) {
-    const int nxt = it + S - 1;
-    if (tid < 32 && nxt < my_tiles) batch_issue<PX>(a, smem, bars, nxt, first + nxt * step, lane);
-    const int g = first + it * step;
-    const int ei = entry_of(a, g);
-    const BatchEntry& e = a.e[ei];
-    const int64_t p0 = static_cast<int64_t>(g - e.tile0) * T;
-    wrs::draw_tile_uniforms<T>(e.s, e.f, p0, ubuf, tid);
-    const int stg = it % S;
-    const bool landed = wrs::mbar_wait_bounded(&bars[stg], (it / S) & 1u, a.timeout_ns);
-    if (!__syncthreads_and(landed)) {
-      ok = false;
-      failed_entry = ei;
-      break;
-    }
-    const bool resolve = e.f.out != nullptr;
-    const uint8_t* st = smem + stg * a.stage_bytes;
-    const float d_f = wrs::fovea_density(e.s);
-    switch (e.code) {
-      case 0: wrs::compute_tile<4, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 2, resolve), st, ubuf, p0, d_f, tid); break;
-      case 1: wrs::compute_tile<8, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 2, resolve), st, ubuf, p0, d_f, tid); break;
-      case 2: wrs::compute_tile<4, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 4, resolve), st, ubuf, p0, d_f, tid); break;
-      case 3: wrs::compute_tile<8, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 4, resolve), st, ubuf, p0, d_f, tid); break;
-      case 4: wrs::compute_tile<0, true, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 2, resolve), st, ubuf, p0, d_f, tid); break;
-      default: wrs::compute_tile<0, false, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 4, resolve), st, ubuf, p0, d_f, tid); break;
-    }
-    __syncthreads();
+  int issued = 0;
+  if (warp == kConsumerWarps) {
+    issued = wrs::produce(r, my_tiles, a.timeout_ns, lane,
+                          [&](int it, uint8_t* st, float* u, uint64_t* full, int ln) {
+                            const int g = first + it * step;
+                            const BatchEntry& e = a.e[entry_of(a, g)];
+                            const int64_t p0 = static_cast<int64_t>(g - e.tile0) * T;
+                            const int cs = entry_f16(e) ? 2 : 4;
+                            const bool resolve = e.f.out != nullptr;
+                            const StageLayout L = wrs::stage_layout(T, e.s.K, cs, resolve);
+                            wrs::draw_tile_uniforms_warp<T>(e.s, e.f, p0, u, ln);
+                            __syncwarp();
+                            wrs::issue_tile_copies<T>(e.s, e.f, e.s.K, cs, resolve, L, st, full,
+                                                      p0, 0u, ln);
+                          });
+  } else {
+    wrs::consume(r, my_tiles, a.timeout_ns, lane, [&](int it, const uint8_t* st, const float* u) {
+      const int g = first + it * step;
+      const BatchEntry& e = a.e[entry_of(a, g)];
+      const int64_t p0 = static_cast<int64_t>(g - e.tile0) * T;
+      const bool resolve = e.f.out != nullptr;
+      const float d_f = wrs::fovea_density(e.s);
+      switch (e.code) {
+        case 0: wrs::compute_tile<4, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 2, resolve), st, u, p0, d_f, tid); break;
+        case 1: wrs::compute_tile<8, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 2, resolve), st, u, p0, d_f, tid); break;
+        case 2: wrs::compute_tile<4, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 4, resolve), st, u, p0, d_f, tid); break;
+        case 3: wrs::compute_tile<8, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 4, resolve), st, u, p0, d_f, tid); break;
+        case 4: wrs::compute_tile<0, true, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 2, resolve), st, u, p0, d_f, tid); break;
+        default: wrs::compute_tile<0, false, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 4, resolve), st, u, p0, d_f, tid); break;
+      }
+    });
   }
-  if (!ok) {
-    if (tid == 0) atomicExch(a.e[failed_entry].status, static_cast<uint32_t>(WRS_ERR_TIMEOUT));
-    const int last = min(it + S, my_tiles);
-    for (int j = it; j < last; ++j)
-      wrs::mbar_wait_bounded(&bars[j % S], (j / S) & 1u, a.timeout_ns);
+  __syncthreads();
+  if (wrs::flag_raised(r)) {
+    if (warp == kConsumerWarps) wrs::drain(r, issued, a.timeout_ns);
+    // the batch ran out of time as a whole: report it on every stream
+    if (tid < a.n) atomicExch(a.e[tid].status, static_cast<uint32_t>(WRS_ERR_TIMEOUT));
   }
 }
 
@@ -275,18 +260,16 @@ extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
     e.tile0 = static_cast<int>(tiles);
     e.code = code_of(x->cfg);
     tiles += (static_cast<int64_t>(e.s.hw) + T - 1) / T;
-    const size_t sb = wrs_pipe_smem_bytes(x->cfg.K, x->cfg.color_fp16 != 0, b->px, 1, out != nullptr) -
-                      4u * T - 8u;  // one stage
-    if (sb > stage_bytes) stage_bytes = static_cast<uint32_t>(sb);
+    const uint32_t sb = wrs::stage_layout(T, x->cfg.K, x->cfg.color_fp16 ? 2 : 4, out != nullptr).bytes;
+    if (sb > stage_bytes) stage_bytes = sb;
   }
   if (tiles > 0x7FFFFFFF) return wrs_fail(WRS_ERR_ARG, "batch too large");
   int stages = b->stages;
   if (stages == 0) {
     stages = 2;
-    while (stages > 1 && static_cast<size_t>(stages) * stage_bytes + 4u * T + 8u * stages > kSmemBudget)
-      --stages;
+    while (stages > 1 && wrs::ring_bytes(stage_bytes, T, stages) > kSmemBudget) --stages;
   }
-  const size_t smem = static_cast<size_t>(stages) * stage_bytes + 4u * T + 8u * stages;
+  const size_t smem = wrs::ring_bytes(stage_bytes, T, stages);
   if (smem > kSmemBudget)
     return wrs_fail(WRS_ERR_ARG, "%d stages of %u B exceed shared memory", stages, stage_bytes);
   a.n = n;
@@ -315,7 +298,7 @@ extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
     b->configured_smem[slot] = smem;
   }
   int fit = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, 256, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, kBatchThreads, smem);
   if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_batch: occupancy");
   if (fit < 1) return wrs_fail(WRS_ERR_ARG, "batch kernel does not fit on an SM");
   const int per_sm = b->ctas_per_sm > 0 && b->ctas_per_sm < fit ? b->ctas_per_sm : fit;
@@ -327,7 +310,7 @@ extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
   void* params[1] = {&a};
   kp.func = const_cast<void*>(fn);
   kp.gridDim = dim3(grid);
-  kp.blockDim = dim3(256);
+  kp.blockDim = dim3(kBatchThreads);
   kp.sharedMemBytes = static_cast<unsigned>(smem);
   kp.kernelParams = params;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);

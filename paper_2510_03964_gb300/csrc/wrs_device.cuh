@@ -142,6 +142,7 @@ struct StreamDev {
   void* col;         // [3][K][plane] float or __half
   int64_t plane;     // entries per plane (multiple of 64)
   int32_t width, height, K, hw;
+  uint32_t width_rcp; // ceil(2^32 / width) (0xFFFFFFFF for width 1): see row_of
   float r_f;         // fovea radius, px
   float delta;       // degrees per px
   uint32_t seed_lo, seed_hi, stream_id;
@@ -156,6 +157,22 @@ struct FrameDev {
   float gx, gy;
   uint32_t t;
 };
+
+// (y, x) of pixel p: y = p / width by a multiply-high with ceil(2^32 / width),
+// which is off by at most one, then corrected with the remainder.
+__device__ __forceinline__ void row_col(const StreamDev& s, int p, int& y, int& x) {
+  int q = static_cast<int>(__umulhi(static_cast<uint32_t>(p), s.width_rcp));
+  int r = p - q * s.width;
+  if (r < 0) {
+    q -= 1;
+    r += s.width;
+  } else if (r >= s.width) {
+    q += 1;
+    r -= s.width;
+  }
+  y = q;
+  x = r;
+}
 
 // density at the fovea edge, the normaliser of Eq. (phat)
 __device__ __forceinline__ float fovea_density(const StreamDev& s) {
@@ -283,8 +300,8 @@ __device__ __forceinline__ Src global_src(const StreamDev& s, const FrameDev& f,
   r.frame = nullptr;
   r.u = nullptr;
   if (vec) {
-    const int y = p0 / s.width;
-    const int x = p0 - y * s.width;
+    int y, x;
+    row_col(s, p0, y, x);
     r.frame = f.frame + static_cast<int64_t>(y) * f.pitch + 3 * x;
   }
   return r;
@@ -357,8 +374,8 @@ __device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f
   bool valid[PX];
   int xs[PX], ys[PX];
   if constexpr (VEC) {
-    const int y = p0 / s.width;
-    const int x = p0 - y * s.width;
+    int y, x;
+    row_col(s, p0, y, x);
 #pragma unroll
     for (int i = 0; i < PX; ++i) {
       valid[i] = true;
@@ -370,8 +387,9 @@ __device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f
     for (int i = 0; i < PX; ++i) {
       const int p = p0 + i;
       valid[i] = p < s.hw;
-      ys[i] = valid[i] ? p / s.width : 0;
-      xs[i] = valid[i] ? p - ys[i] * s.width : 0;
+      ys[i] = 0;
+      xs[i] = 0;
+      if (valid[i]) row_col(s, p, ys[i], xs[i]);
     }
   }
 

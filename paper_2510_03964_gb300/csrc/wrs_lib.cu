@@ -100,6 +100,9 @@ StreamDev wrs_stream_dev(const wrs_ctx* x) {
   s.height = x->cfg.height;
   s.K = x->cfg.K;
   s.hw = x->cfg.width * x->cfg.height;
+  s.width_rcp = x->cfg.width == 1
+                    ? 0xFFFFFFFFu
+                    : static_cast<uint32_t>(((1ull << 32) + x->cfg.width - 1) / x->cfg.width);
   s.r_f = x->cfg.fovea_radius_px;
   s.delta = wrs_delta(&x->cfg);
   s.seed_lo = static_cast<uint32_t>(x->cfg.seed);

@@ -1,15 +1,16 @@
 // Pipelined persistent form of the fused update + resolve (sm_103a).
 //
 // Persistent CTAs (one or more per SM) walk the image in tiles of
-// T = 256 * PX pixels. Warp 0 streams the planes a tile needs (frame RGB, W,
-// P, the K key planes and, for the fused resolve, the K weight and 3K colour
-// planes) into a ring of S shared-memory stages with 1-D bulk asynchronous
-// copies (cp.async.bulk) that complete on one transaction-count mbarrier per
-// stage. While a tile's copies are in flight its uniforms are drawn (one
-// Philox block per 4 pixels, by T/4 threads) into shared memory; then all 256
-// threads compute the tile from shared memory with the same per-pixel code as
-// the plain kernel (bit-identical results). Writes go straight to global
-// memory.
+// T = 256 * PX pixels. A producer warp streams the planes a tile needs (frame
+// RGB, W, P, the K key planes and, for the fused resolve, the K weight and 3K
+// colour planes) into a ring of S shared-memory stages with 1-D bulk
+// asynchronous copies (cp.async.bulk) that complete on one transaction-count
+// "full" mbarrier per stage, after drawing the tile's uniforms (one Philox
+// block per 4 pixels) into the stage. Eight consumer warps compute each
+// landed tile from shared memory with the same per-pixel code as the plain
+// kernel (bit-identical results), write straight to global memory and free
+// the stage through its "empty" mbarrier. No block-wide barrier sits inside
+// the loop.
 //
 // Every wait is bounded by %globaltimer. A wait that runs out records
 // WRS_ERR_TIMEOUT in the stream's status word, waits (again bounded) for the
@@ -37,81 +38,62 @@ struct PipeArgs {
   uint32_t extra_tx;       // added to the expected bytes: > 0 only to test the timeout path
 };
 
-// dynamic shared memory: S stages | uniforms [T] | S barriers
-__host__ __device__ __forceinline__ size_t pipe_smem_bytes(const StageLayout& L, int T, int S) {
-  return static_cast<size_t>(S) * L.bytes + 4u * T + 8u * S;
-}
+constexpr int kConsumerWarps = 8;
+constexpr int kPipeThreads = (kConsumerWarps + 1) * 32;
 
+// Warp-specialised: warps 0..7 compute (consumers, PX pixels per thread), warp 8
+// draws uniforms and issues copies (producer). Consumers and producer meet
+// only at the per-stage full/empty barriers, never at a block-wide barrier.
 template <int KT, bool F16, int PX>
-__global__ void __launch_bounds__(256, PX == 1 ? 2 : 1)
+__global__ void __launch_bounds__(kPipeThreads, PX == 1 ? 2 : 1)
     pipe_kernel(const __grid_constant__ StreamDev s, const __grid_constant__ FrameDev f,
                 const PipeArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
-  constexpr int T = 256 * PX;
+  constexpr int T = kConsumerWarps * 32 * PX;
   constexpr int cs = F16 ? 2 : 4;
   const int K = KT > 0 ? KT : s.K;
-  const int S = a.stages;
-  const StageLayout L = wrs::stage_layout(T, K, cs, a.resolve != 0);
-  float* ubuf = reinterpret_cast<float*>(smem + S * L.bytes);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * L.bytes + 4 * T);
+  const bool resolve = a.resolve != 0;
+  const StageLayout L = wrs::stage_layout(T, K, cs, resolve);
+  const wrs::Ring r = wrs::make_ring(smem, L.bytes, T, a.stages);
   const int tid = threadIdx.x;
+  const int warp = tid >> 5;
   const int lane = tid & 31;
-
-  if (tid == 0) {
-    for (int i = 0; i < S; ++i) wrs::mbar_init(&bars[i], 1);
-    wrs::fence_mbar_init();
-  }
+  if (tid == 0) wrs::init_ring(r, kConsumerWarps);
   __syncthreads();
 
   const int first = blockIdx.x;
   const int step = gridDim.x;
   const int my_tiles = first < a.ntiles ? (a.ntiles - 1 - first) / step + 1 : 0;
-  const int prologue = min(S - 1, my_tiles);
-  if (tid < 32)
-    for (int it = 0; it < prologue; ++it)
-      wrs::issue_tile_copies<T>(s, f, K, cs, a.resolve != 0, L, smem + (it % S) * L.bytes,
-                                &bars[it % S], static_cast<int64_t>(first + it * step) * T,
-                                a.extra_tx, lane);
-
-  const float d_f = wrs::fovea_density(s);
-  int it = 0;
-  bool ok = true;
-  for (; it < my_tiles; ++it) {
-    const int nxt = it + S - 1;
-    if (tid < 32 && nxt < my_tiles)
-      wrs::issue_tile_copies<T>(s, f, K, cs, a.resolve != 0, L, smem + (nxt % S) * L.bytes,
-                                &bars[nxt % S], static_cast<int64_t>(first + nxt * step) * T,
-                                a.extra_tx, lane);
-    const int64_t p0 = static_cast<int64_t>(first + it * step) * T;
-    wrs::draw_tile_uniforms<T>(s, f, p0, ubuf, tid);
-    const int stg = it % S;
-    // every thread waits; the block then agrees on the outcome (this barrier
-    // also publishes the uniforms), so no thread leaves the loop while others
-    // wait at a barrier
-    const bool landed = wrs::mbar_wait_bounded(&bars[stg], (it / S) & 1u, a.timeout_ns);
-    if (!__syncthreads_and(landed)) {
-      ok = false;
-      break;
-    }
-    wrs::compute_tile<KT, F16, PX, T>(s, f, L, smem + stg * L.bytes, ubuf, p0, d_f, tid);
-    __syncthreads();
+  int issued = 0;
+  if (warp == kConsumerWarps) {
+    issued = wrs::produce(r, my_tiles, a.timeout_ns, lane,
+                          [&](int it, uint8_t* st, float* u, uint64_t* full, int ln) {
+                            const int64_t p0 = static_cast<int64_t>(first + it * step) * T;
+                            wrs::draw_tile_uniforms_warp<T>(s, f, p0, u, ln);
+                            __syncwarp();
+                            wrs::issue_tile_copies<T>(s, f, K, cs, resolve, L, st, full, p0,
+                                                      a.extra_tx, ln);
+                          });
+  } else {
+    const float d_f = wrs::fovea_density(s);
+    wrs::consume(r, my_tiles, a.timeout_ns, lane, [&](int it, const uint8_t* st, const float* u) {
+      const int64_t p0 = static_cast<int64_t>(first + it * step) * T;
+      wrs::compute_tile<KT, F16, PX, T>(s, f, L, st, u, p0, d_f, tid);
+    });
   }
-  if (!ok) {
-    // record the timeout, then let every copy this CTA issued land before the
-    // shared memory is released: tiles it .. min(it + S - 1, my_tiles - 1)
+  __syncthreads();
+  if (wrs::flag_raised(r)) {
+    if (warp == kConsumerWarps) wrs::drain(r, issued, a.timeout_ns);
     if (tid == 0) atomicExch(a.status, static_cast<uint32_t>(WRS_ERR_TIMEOUT));
-    const int last = min(it + S, my_tiles);
-    for (int j = it; j < last; ++j)
-      wrs::mbar_wait_bounded(&bars[j % S], (j / S) & 1u, a.timeout_ns);
   }
 }
 
 template <int KT, bool F16, int PX>
 cudaError_t launch_pipe_t(const StreamDev& s, const FrameDev& f, PipeArgs a, int sms,
                           int ctas_per_sm, cudaStream_t st) {
-  constexpr int T = 256 * PX;
+  constexpr int T = kConsumerWarps * 32 * PX;
   const StageLayout L = wrs::stage_layout(T, s.K, F16 ? 2 : 4, a.resolve != 0);
-  const size_t smem = pipe_smem_bytes(L, T, a.stages);
+  const size_t smem = wrs::ring_bytes(L.bytes, T, a.stages);
   // per instantiation and device: the largest dynamic shared memory already allowed
   static size_t configured[64] = {};
   int dev = 0;
@@ -125,14 +107,15 @@ cudaError_t launch_pipe_t(const StreamDev& s, const FrameDev& f, PipeArgs a, int
     configured[dev] = smem;
   }
   int fit = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, pipe_kernel<KT, F16, PX>, 256, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, pipe_kernel<KT, F16, PX>, kPipeThreads,
+                                                    smem);
   if (e != cudaSuccess) return e;
   if (fit < 1) return cudaErrorInvalidConfiguration;
   const int per_sm = ctas_per_sm > 0 && ctas_per_sm < fit ? ctas_per_sm : fit;
   a.ntiles = static_cast<int>((static_cast<int64_t>(s.hw) + T - 1) / T);
   const int64_t want = static_cast<int64_t>(sms) * per_sm;
   const int grid = static_cast<int>(a.ntiles < want ? a.ntiles : want);
-  pipe_kernel<KT, F16, PX><<<grid, 256, smem, st>>>(s, f, a);
+  pipe_kernel<KT, F16, PX><<<grid, kPipeThreads, smem, st>>>(s, f, a);
   return cudaGetLastError();
 }
 
@@ -162,8 +145,8 @@ cudaError_t launch_pipe_k(const StreamDev& s, const FrameDev& f, const PipeArgs&
 
 // Shared memory one CTA of the pipelined kernel needs.
 size_t wrs_pipe_smem_bytes(int K, bool f16, int px, int stages, bool resolve) {
-  const int T = 256 * px;
-  return pipe_smem_bytes(wrs::stage_layout(T, K, f16 ? 2 : 4, resolve), T, stages);
+  const int T = kConsumerWarps * 32 * px;
+  return wrs::ring_bytes(wrs::stage_layout(T, K, f16 ? 2 : 4, resolve).bytes, T, stages);
 }
 
 bool wrs_pipe_supported(const wrs_ctx* x, const float* frame, int64_t pitch, const float* out) {
