@@ -17,6 +17,19 @@ MIX = [  # width, height, K, fp16, r_f
 ]
 
 
+SMEM_BUDGET = 227 * 1024 - 1024
+
+
+def _fits(specs, px, stages):
+    """Whether the batched kernel's shared-memory ring fits (same sizes as the library)."""
+    T = 256 * px
+    stage = max(T * (20 + 8 * K + 3 * K * (2 if f16 else 4)) for (w, h, K, f16, rf) in specs)
+    S = stages or 2
+    while stages == 0 and S > 1 and S * (stage + 4 * T) + 16 * S + 16 > SMEM_BUDGET:
+        S -= 1
+    return S * (stage + 4 * T) + 16 * S + 16 <= SMEM_BUDGET
+
+
 def _streams(dev, specs, seed0=1):
     out = []
     for i, (w, h, K, f16, rf) in enumerate(specs):
@@ -37,6 +50,15 @@ def _frames(specs, frames, seed0=1, dev="cuda"):
                                     (4, 1, 0, False), (1, 3, 2, False), (2, 1, 1, True)])
 def test_batch_equals_individual_pushes(launch):
     dev = torch.device("cuda")
+    if not _fits(MIX, launch[0], launch[1]):
+        b = wrs.Batch(16)
+        b.set_launch(*launch)
+        st = _streams(dev, MIX)
+        data = _frames(MIX, 1)
+        with pytest.raises(wrs.WrsError, match="shared memory"):
+            b.push(st, [d[0][0] for d in data], [d[0][1] for d in data])
+        assert all(x.frame_index == 0 for x in st)
+        return
     frames = 7
     data = _frames(MIX, frames)
     solo = _streams(dev, MIX)

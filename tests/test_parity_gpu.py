@@ -65,7 +65,8 @@ def test_pipeline_shapes_agree(pipeline, K, fp16):
     kernel give the same planes."""
     enable, px, stages, _ = pipeline
     cs = 2 if fp16 else 4
-    if enable and stages * 256 * px * (20 + 8 * K + 3 * K * cs) + 1024 * px + 64 > 226 * 1024:
+    T = 256 * px
+    if enable and stages * (T * (20 + 8 * K + 3 * K * cs) + 4 * T) + 16 * stages + 16 > 227 * 1024 - 1024:
         pytest.skip("these stages do not fit in shared memory (rejected by wrs_set_pipeline)")
     run = PairedRun(96, 40, K, r_f=10.0, frames=12, seed=5, jitter_px=20, color_fp16=fp16,
                     pipeline=pipeline)
