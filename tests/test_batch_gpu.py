@@ -21,7 +21,8 @@ SMEM_BUDGET = 227 * 1024 - 1024
 
 
 def _fits(specs, px, stages):
-    """Whether the batched kernel's shared-memory ring fits (same sizes as the library)."""
+    """Whether the batched kernel's shared-memory ring fits with fused resolves
+    (same sizes as the library)."""
     T = 256 * px
     stage = max(T * (20 + 8 * K + 3 * K * (2 if f16 else 4)) for (w, h, K, f16, rf) in specs)
     S = stages or 2
@@ -55,8 +56,9 @@ def test_batch_equals_individual_pushes(launch):
         b.set_launch(*launch)
         st = _streams(dev, MIX)
         data = _frames(MIX, 1)
+        outs = [torch.empty((h, w, 3), device=dev) for (w, h, *_r) in MIX]
         with pytest.raises(wrs.WrsError, match="shared memory"):
-            b.push(st, [d[0][0] for d in data], [d[0][1] for d in data])
+            b.push(st, [d[0][0] for d in data], [d[0][1] for d in data], outs=outs)
         assert all(x.frame_index == 0 for x in st)
         return
     frames = 7
