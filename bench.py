@@ -36,12 +36,16 @@ UNIT = "ms/frame"
 
 
 def algorithmic_bytes_per_px(K: int, fp16: bool) -> int:
-    """Bytes one pixel-update must move: frame RGB in (12), resolved RGB out
+    """Bytes every pixel-update moves: frame RGB in (12), resolved RGB out
     (12), W and P read and written (16), every slot's key, weight and colour
-    read (K * (8 + 3c)); replacement writes excluded (they depend on the
-    stream)."""
+    read (K * (8 + 3c))."""
     c = 2 if fp16 else 4
     return 40 + K * (8 + 3 * c)
+
+
+def replacement_bytes(fp16: bool) -> int:
+    """Bytes a replacement writes: key, sample index, weight and colour of the slot."""
+    return 12 + (6 if fp16 else 12)
 
 
 # ------------------------------------------------------------------ clocks
@@ -280,6 +284,7 @@ def run_ours(args, world, rank, local):
 
     clocks = ClockSampler(local) if rank == 0 else None
     time.sleep(0.3 if clocks else 0.0)
+    repl0 = st.replacements(stream=stream)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier(world)
@@ -292,6 +297,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop() if clocks else None
+    rho = (st.replacements(stream=stream) - repl0) / float(hw * args.steps)
     total_ms = starts[0].elapsed_time(ends[-1])
     kernel_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = max_over_ranks(world, total_ms, dev)
@@ -333,7 +339,7 @@ def run_ours(args, world, rank, local):
         return
 
     peaks = measured_peaks()
-    bpp = algorithmic_bytes_per_px(spec.K, spec.color_fp16)
+    bpp = algorithmic_bytes_per_px(spec.K, spec.color_fp16) + rho * replacement_bytes(spec.color_fp16)
     achieved = bpp * hw / (kernel_avg * 1e-3) / 1e9
     kname = (f"{'pipe_kernel' if st.get_pipeline()[0] else 'push_kernel'}"
              f"<K={spec.K},{'fp16' if spec.color_fp16 else 'fp32'}>")
@@ -357,7 +363,12 @@ def run_ours(args, world, rank, local):
                      "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
                      "traffic": recorded_traffic(kname, args.workload),
                      "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs, copy)",
-                     "algorithmic_bytes_per_px": bpp, "kernel": kname},
+                     "algorithmic_bytes_per_px": round(bpp, 2),
+                     "bytes_rule": f"{algorithmic_bytes_per_px(spec.K, spec.color_fp16)} B read/written by "
+                                   f"every pixel-update + replacement rate {rho:.4f} (counted on the device "
+                                   f"over the timed frames) x {replacement_bytes(spec.color_fp16)} B",
+                     "kernel": kname},
+        "replacement_rate": round(rho, 4),
         "pct_nominal_8tbs": round(100 * achieved / 8000.0, 2),
         "gpu_launches": args.steps,
         "clocks": clk,
@@ -382,7 +393,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="4k", choices=["4k", "4k_fp16", "hd"])
+    ap.add_argument("--workload", default="4k", choices=["4k", "4k_fp16", "hd", "hd_k8"])
     ap.add_argument("--distinct-frames", type=int, default=0,
                     help="frames resident in HBM (default: all of the workload's)")
     ap.add_argument("--pipe", type=int, default=1, help="1: pipelined kernel (default), 0: plain")

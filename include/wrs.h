@@ -76,15 +76,21 @@ typedef struct {
  *   W        float   running weight sum R.wsum (Alg. 2), biased (Eq. (temporal-bias))
  *   P        float   product of bias factors since the last rescale
  *   key[j]   float   stored key of slot j (+inf when empty), at key_off + j*plane_bytes4
- *   idx[j]   uint32  frame index of the slot's sample (WRS_EMPTY_SLOT when empty)
- *   wt[j]    float   perceptual weight w of the slot's sample (0 when empty)
- *   col[c][j] float or half  colour channel c of slot j, at
- *                    col_off + (c*K + j) * plane_bytes_col (0 when empty) */
+ *   idx[j]   uint32  frame index of the slot's sample (WRS_EMPTY_SLOT when empty),
+ *                    at idx_off + j*plane_bytes4
+ * and the slot weights w (perceptual weight of the slot's sample) and colours,
+ * 0 when empty:
+ *   FP32 colour: rec[j] float4 {w, r, g, b} at col_off + j*plane_bytes_col
+ *                (plane_bytes_col = 16*plane_px; wt_off = -1). One record per
+ *                slot keeps a replacement's writes in one 16-byte entry.
+ *   FP16 colour: wt[j] float at wt_off + j*plane_bytes4 and col[c][j] half at
+ *                col_off + (c*K + j)*plane_bytes_col (plane_bytes_col = 2*plane_px). */
 typedef struct {
   int64_t plane_px;
   int64_t plane_bytes4;     /* plane_px * 4 */
   int64_t plane_bytes_col;  /* plane_px * 4 (FP32 colour) or * 2 (FP16 colour) */
-  int64_t status_off;       /* uint32 status word (WRS_OK or WRS_ERR_TIMEOUT), 256-byte header */
+  int64_t status_off;       /* 256-byte header: uint32 status word (WRS_OK or WRS_ERR_TIMEOUT)
+                               at +0, uint64 count of slot replacements at +8 */
   int64_t W_off, P_off, key_off, idx_off, wt_off, col_off;
   int64_t total_bytes;
 } wrs_layout;
@@ -215,6 +221,11 @@ int wrs_batch_get_launch(const wrs_batch* batch, int* px_per_thread, int* stages
 int wrs_push_batch(wrs_batch* batch, int n, wrs_ctx* const* ctxs, const float* const* d_frames,
                    const float* gaze_xy, const uint8_t* const* d_fov_maps, float* const* d_outs,
                    wrs_stream_t stream);
+
+/* Slot replacements since create (over all pixels and frames; the stream's
+ * reservoir churn: a pixel whose candidate entered a slot counts once per
+ * frame). Waits for `stream`. */
+int wrs_get_stats(wrs_ctx* ctx, uint64_t* replacements, wrs_stream_t stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* wrs_last_error(void);

@@ -52,6 +52,7 @@ SIGNATURES = {
     "wrs_batch_set_launch": (_I, [_V, _I, _I, _I, _I]),
     "wrs_batch_get_launch": (_I, [_V, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "wrs_push_batch": (_I, [_V, _I, _V, _V, _V, _V, _V, _V]),
+    "wrs_get_stats": (_I, [_V, C.POINTER(C.c_uint64), _V]),
     "wrs_last_error": (C.c_char_p, []),
 }
 

@@ -71,6 +71,8 @@ static __device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t pa
 }
 
 // Byte offsets of one stage's planes in shared memory (tile of T pixels).
+// cs = 2 (FP16 colour: weight plane + 3K half planes) or 4 (FP32 colour: K
+// float4 {w, r, g, b} record planes, starting at `col`; `wt` == `col`).
 struct StageLayout {
   uint32_t frame, W, P, key, wt, col, bytes;
 };
@@ -81,9 +83,14 @@ __host__ __device__ __forceinline__ StageLayout stage_layout(int T, int K, int c
   L.W = 12u * T;
   L.P = L.W + 4u * T;
   L.key = L.P + 4u * T;
-  L.wt = L.key + 4u * K * T;
-  L.col = L.wt + (resolve ? 4u * K * T : 0u);
-  L.bytes = L.col + (resolve ? static_cast<uint32_t>(cs) * 3u * K * T : 0u);
+  if (cs == 2) {
+    L.wt = L.key + 4u * K * T;
+    L.col = L.wt + (resolve ? 4u * K * T : 0u);
+    L.bytes = L.col + (resolve ? 2u * 3u * K * T : 0u);
+  } else {
+    L.wt = L.col = L.key + 4u * K * T;
+    L.bytes = L.col + (resolve ? 16u * K * T : 0u);
+  }
   return L;
 }
 
@@ -100,10 +107,10 @@ __device__ __forceinline__ void issue_tile_copies(const StreamDev& s, const Fram
   const int64_t rem_plane = s.plane - p0, rem_px = s.hw - p0;
   const uint32_t n = static_cast<uint32_t>(rem_plane < T ? rem_plane : T);  // plane entries (x64)
   const uint32_t np = static_cast<uint32_t>(rem_px < T ? rem_px : T);       // pixels (x4)
-  const int ncopy = 3 + K + (resolve ? 4 * K : 0);
+  const int ncopy = 3 + K + (resolve ? (cs == 2 ? 4 * K : K) : 0);
   if (lane == 0) {
     uint32_t bytes = 12u * np + 8u * n + 4u * K * n;
-    if (resolve) bytes += 4u * K * n + static_cast<uint32_t>(cs) * 3u * K * n;
+    if (resolve) bytes += cs == 2 ? (4u * K * n + 2u * 3u * K * n) : 16u * K * n;
     mbar_arrive_expect_tx(bar, bytes + extra_tx);
   }
   __syncwarp();
@@ -118,6 +125,10 @@ __device__ __forceinline__ void issue_tile_copies(const StreamDev& s, const Fram
     } else if (c < 3 + K) {
       const int j = c - 3;
       bulk_g2s(stage + L.key + 4u * T * j, s.key + j * pl + p0, 4u * n, bar);
+    } else if (cs == 4) {
+      const int j = c - 3 - K;  // FP32 colour: record plane j
+      bulk_g2s(stage + L.col + 16u * T * j,
+               static_cast<const float4*>(s.col) + j * pl + p0, 16u * n, bar);
     } else if (c < 3 + 2 * K) {
       const int j = c - 3 - K;
       bulk_g2s(stage + L.wt + 4u * T * j, s.wt + j * pl + p0, 4u * n, bar);
@@ -147,14 +158,15 @@ __device__ __forceinline__ void draw_tile_uniforms_warp(const StreamDev& s, cons
   }
 }
 
-// Computes consumer thread `tid`'s PX pixels of a landed tile from shared memory.
+// Computes consumer thread `tid`'s PX pixels of a landed tile from shared
+// memory; returns how many of them replaced a slot.
 template <int KT, bool F16, int PX, int T>
-__device__ __forceinline__ void compute_tile(const StreamDev& s, const FrameDev& f,
-                                             const StageLayout& L, const uint8_t* st,
-                                             const float* u, int64_t p0, float d_f, int tid) {
+__device__ __forceinline__ int compute_tile(const StreamDev& s, const FrameDev& f,
+                                            const StageLayout& L, const uint8_t* st,
+                                            const float* u, int64_t p0, float d_f, int tid) {
   const int tl = tid * PX;
   const int64_t p = p0 + tl;
-  if (p >= s.hw) return;
+  if (p >= s.hw) return 0;
   Src src;
   src.W = reinterpret_cast<const float*>(st + L.W);
   src.P = reinterpret_cast<const float*>(st + L.P);
@@ -165,10 +177,14 @@ __device__ __forceinline__ void compute_tile(const StreamDev& s, const FrameDev&
   src.at = tl;
   src.frame = reinterpret_cast<const float*>(st + L.frame) + 3 * tl;
   src.u = u + tl;
-  if (f.fov != nullptr)
-    push_group<KT, F16, PX, true, true>(s, f, static_cast<int>(p), src, d_f);
-  else
-    push_group<KT, F16, PX, true, false>(s, f, static_cast<int>(p), src, d_f);
+  if (f.fov != nullptr) return push_group<KT, F16, PX, true, true>(s, f, static_cast<int>(p), src, d_f);
+  return push_group<KT, F16, PX, true, false>(s, f, static_cast<int>(p), src, d_f);
+}
+
+// Adds a warp's counts to a running total: one atomic per warp.
+__device__ __forceinline__ void add_warp_count(unsigned long long* total, int count, int lane) {
+  const unsigned c = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(count));
+  if (lane == 0 && c != 0) atomicAdd(total, static_cast<unsigned long long>(c));
 }
 
 // ---------------------------------------------------------------- warp-specialised loop

@@ -70,12 +70,14 @@ template <int PX>
 __global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
     batch_kernel(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ unsigned long long replaced_s[kMaxBatch];  // per stream, this CTA
   constexpr int T = kConsumerWarps * 32 * PX;
   const wrs::Ring r = wrs::make_ring(smem, a.stage_bytes, T, a.stages);
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
   if (tid == 0) wrs::init_ring(r, kConsumerWarps);
+  if (tid < kMaxBatch) replaced_s[tid] = 0;
   __syncthreads();
 
   const int first = blockIdx.x, step = gridDim.x;
@@ -102,17 +104,21 @@ __global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
       const int64_t p0 = static_cast<int64_t>(g - e.tile0) * T;
       const bool resolve = e.f.out != nullptr;
       const float d_f = wrs::fovea_density(e.s);
+      int rc;
       switch (e.code) {
-        case 0: wrs::compute_tile<4, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 2, resolve), st, u, p0, d_f, tid); break;
-        case 1: wrs::compute_tile<8, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 2, resolve), st, u, p0, d_f, tid); break;
-        case 2: wrs::compute_tile<4, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 4, resolve), st, u, p0, d_f, tid); break;
-        case 3: wrs::compute_tile<8, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 4, resolve), st, u, p0, d_f, tid); break;
-        case 4: wrs::compute_tile<0, true, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 2, resolve), st, u, p0, d_f, tid); break;
-        default: wrs::compute_tile<0, false, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 4, resolve), st, u, p0, d_f, tid); break;
+        case 0: rc = wrs::compute_tile<4, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 2, resolve), st, u, p0, d_f, tid); break;
+        case 1: rc = wrs::compute_tile<8, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 2, resolve), st, u, p0, d_f, tid); break;
+        case 2: rc = wrs::compute_tile<4, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 4, resolve), st, u, p0, d_f, tid); break;
+        case 3: rc = wrs::compute_tile<8, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 4, resolve), st, u, p0, d_f, tid); break;
+        case 4: rc = wrs::compute_tile<0, true, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 2, resolve), st, u, p0, d_f, tid); break;
+        default: rc = wrs::compute_tile<0, false, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 4, resolve), st, u, p0, d_f, tid); break;
       }
+      const unsigned c = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(rc));
+      if (lane == 0 && c != 0) atomicAdd(&replaced_s[entry_of(a, g)], static_cast<unsigned long long>(c));
     });
   }
   __syncthreads();
+  if (tid < a.n && replaced_s[tid] != 0) atomicAdd(a.e[tid].s.replacements, replaced_s[tid]);
   if (wrs::flag_raised(r)) {
     if (warp == kConsumerWarps) wrs::drain(r, issued, a.timeout_ns);
     // the batch ran out of time as a whole: report it on every stream

@@ -138,8 +138,9 @@ struct StreamDev {
   float* P;          // [plane]
   float* key;        // [K][plane]
   uint32_t* idx;     // [K][plane]
-  float* wt;         // [K][plane]
-  void* col;         // [3][K][plane] float or __half
+  float* wt;         // FP16 colour: [K][plane] slot weights; FP32 colour: unused
+  void* col;         // FP16 colour: [3][K][plane] __half; FP32 colour: [K][plane] float4
+                     // records {w, r, g, b} (weight and colour of a slot in one 16-byte entry)
   int64_t plane;     // entries per plane (multiple of 64)
   int32_t width, height, K, hw;
   uint32_t width_rcp; // ceil(2^32 / width) (0xFFFFFFFF for width 1): see row_of
@@ -147,6 +148,7 @@ struct StreamDev {
   float delta;       // degrees per px
   uint32_t seed_lo, seed_hi, stream_id;
   int32_t bias;
+  unsigned long long* replacements;  // running count of slot replacements (stream header)
 };
 
 struct FrameDev {
@@ -239,6 +241,46 @@ template <bool F16>
 __device__ __forceinline__ void store_col(void* base, int64_t off, float v) {
   if constexpr (F16) static_cast<__half*>(base)[off] = __float2half_rn(v);
   else static_cast<float*>(base)[off] = v;
+}
+
+// Weight and colour of slot j for a group of N pixels whose first entry is at
+// `at` in planes of `stride` entries. FP32 colour: one float4 record
+// {w, r, g, b} per entry in `col`; FP16 colour: a weight plane and 3K half
+// planes.
+template <bool F16, int N>
+__device__ __forceinline__ void load_slot(const float* wt, const void* col, int K, int j,
+                                          int64_t stride, int64_t at, float (&a)[N],
+                                          float (&r)[N], float (&g)[N], float (&b)[N]) {
+  if constexpr (F16) {
+    load_f<N>(wt + j * stride + at, a);
+    load_h<N>(static_cast<const __half*>(col) + (0 * K + j) * stride + at, r);
+    load_h<N>(static_cast<const __half*>(col) + (1 * K + j) * stride + at, g);
+    load_h<N>(static_cast<const __half*>(col) + (2 * K + j) * stride + at, b);
+  } else {
+    const float4* rec = static_cast<const float4*>(col) + j * stride + at;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const float4 v = rec[i];
+      a[i] = v.x;
+      r[i] = v.y;
+      g[i] = v.z;
+      b[i] = v.w;
+    }
+  }
+}
+
+// Writes slot j of pixel p (global planes of `plane` entries).
+template <bool F16>
+__device__ __forceinline__ void store_slot(float* wt, void* col, int K, int j, int64_t plane,
+                                           int64_t p, float w, float r, float g, float b) {
+  if constexpr (F16) {
+    wt[j * plane + p] = w;
+    store_col<true>(col, (0 * K + j) * plane + p, r);
+    store_col<true>(col, (1 * K + j) * plane + p, g);
+    store_col<true>(col, (2 * K + j) * plane + p, b);
+  } else {
+    static_cast<float4*>(col)[j * plane + p] = make_float4(w, r, g, b);
+  }
 }
 
 // colour as it will be stored in a slot (FP16 storage rounds to nearest even)
@@ -364,8 +406,8 @@ __device__ __forceinline__ void store_rgb(float* dst, const float (&o)[N][3]) {
 // FOV: a flush map is present (f.fov != null); without one the flush logic is
 // compiled out.
 template <int KT, bool F16, int PX, bool VEC, bool FOV>
-__device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f, int p0,
-                                           const Src& src, float d_f) {
+__device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f, int p0,
+                                          const Src& src, float d_f) {
   const int K = KT > 0 ? KT : s.K;
   const int64_t pl = s.plane;
   const int64_t ss = src.stride;
@@ -484,10 +526,7 @@ __device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f
 #pragma unroll 4
     for (int j = 0; j < K; ++j) {
       float wv[PX], c0[PX], c1[PX], c2[PX];
-      load_f<PX>(src.wt + j * ss + sa, wv);
-      load_colv<F16, PX>(src.col, (0 * K + j) * ss + sa, c0);
-      load_colv<F16, PX>(src.col, (1 * K + j) * ss + sa, c1);
-      load_colv<F16, PX>(src.col, (2 * K + j) * ss + sa, c2);
+      load_slot<F16, PX>(src.wt, src.col, K, j, ss, sa, wv, c0, c1, c2);
 #pragma unroll
       for (int i = 0; i < PX; ++i) {
         float a = wv[i], r = c0[i], g = c1[i], b = c2[i];
@@ -537,22 +576,20 @@ __device__ __forceinline__ void push_group(const StreamDev& s, const FrameDev& f
         if (j == jm[i]) continue;
         s.key[j * pl + p] = kInf;
         s.idx[j * pl + p] = kEmpty;
-        s.wt[j * pl + p] = 0.0f;
-        store_col<F16>(s.col, (0 * K + j) * pl + p, 0.0f);
-        store_col<F16>(s.col, (1 * K + j) * pl + p, 0.0f);
-        store_col<F16>(s.col, (2 * K + j) * pl + p, 0.0f);
+        store_slot<F16>(s.wt, s.col, K, j, pl, p, 0.0f, 0.0f, 0.0f, 0.0f);
       }
     }
     if (repl[i]) {
       const int j = jm[i];
       s.key[j * pl + p] = ks[i];
       s.idx[j * pl + p] = f.t;
-      s.wt[j * pl + p] = w[i];
-      store_col<F16>(s.col, (0 * K + j) * pl + p, rgb[i][0]);
-      store_col<F16>(s.col, (1 * K + j) * pl + p, rgb[i][1]);
-      store_col<F16>(s.col, (2 * K + j) * pl + p, rgb[i][2]);
+      store_slot<F16>(s.wt, s.col, K, j, pl, p, w[i], rgb[i][0], rgb[i][1], rgb[i][2]);
     }
   }
+  int replaced = 0;
+#pragma unroll
+  for (int i = 0; i < PX; ++i) replaced += repl[i] ? 1 : 0;
+  return replaced;
 }
 
 // Standalone resolve of one group: the same accumulation as the fused resolve.
@@ -566,10 +603,7 @@ __device__ __forceinline__ void resolve_group(const StreamDev& s, float* out, in
 #pragma unroll 4
   for (int j = 0; j < K; ++j) {
     float wv[PX], c0[PX], c1[PX], c2[PX];
-    load_f<PX>(s.wt + j * pl + p0, wv);
-    load_colv<F16, PX>(s.col, (0 * K + j) * pl + p0, c0);
-    load_colv<F16, PX>(s.col, (1 * K + j) * pl + p0, c1);
-    load_colv<F16, PX>(s.col, (2 * K + j) * pl + p0, c2);
+    load_slot<F16, PX>(s.wt, s.col, K, j, pl, p0, wv, c0, c1, c2);
 #pragma unroll
     for (int i = 0; i < PX; ++i) {
       num[i][0] = __fmaf_rn(wv[i], c0[i], num[i][0]);

@@ -70,15 +70,22 @@ void wrs_make_layout(const wrs_config* c, wrs_layout* L) {
   const int64_t pl = (hw + kPlaneAlign - 1) / kPlaneAlign * kPlaneAlign;
   L->plane_px = pl;
   L->plane_bytes4 = pl * 4;
-  L->plane_bytes_col = pl * (c->color_fp16 ? 2 : 4);
+  L->plane_bytes_col = pl * (c->color_fp16 ? 2 : 16);
   L->status_off = 0;
   L->W_off = kStatusBytes;
   L->P_off = L->W_off + L->plane_bytes4;
   L->key_off = L->P_off + L->plane_bytes4;
   L->idx_off = L->key_off + c->K * L->plane_bytes4;
-  L->wt_off = L->idx_off + c->K * L->plane_bytes4;
-  L->col_off = L->wt_off + c->K * L->plane_bytes4;
-  L->total_bytes = L->col_off + 3 * c->K * L->plane_bytes_col;
+  if (c->color_fp16) {
+    L->wt_off = L->idx_off + c->K * L->plane_bytes4;
+    L->col_off = L->wt_off + c->K * L->plane_bytes4;
+    L->total_bytes = L->col_off + 3 * c->K * L->plane_bytes_col;
+  } else {
+    // FP32 colour: weight and colour of a slot in one float4 record
+    L->wt_off = -1;
+    L->col_off = L->idx_off + c->K * L->plane_bytes4;
+    L->total_bytes = L->col_off + c->K * L->plane_bytes_col;
+  }
 }
 
 float wrs_delta(const wrs_config* c) {
@@ -93,7 +100,7 @@ StreamDev wrs_stream_dev(const wrs_ctx* x) {
   s.P = reinterpret_cast<float*>(b + x->lay.P_off);
   s.key = reinterpret_cast<float*>(b + x->lay.key_off);
   s.idx = reinterpret_cast<uint32_t*>(b + x->lay.idx_off);
-  s.wt = reinterpret_cast<float*>(b + x->lay.wt_off);
+  s.wt = x->lay.wt_off >= 0 ? reinterpret_cast<float*>(b + x->lay.wt_off) : nullptr;
   s.col = b + x->lay.col_off;
   s.plane = x->lay.plane_px;
   s.width = x->cfg.width;
@@ -109,6 +116,7 @@ StreamDev wrs_stream_dev(const wrs_ctx* x) {
   s.seed_hi = static_cast<uint32_t>(x->cfg.seed >> 32);
   s.stream_id = x->cfg.stream_id;
   s.bias = x->cfg.temporal_bias;
+  s.replacements = reinterpret_cast<unsigned long long*>(x->state + x->lay.status_off + 8);
   return s;
 }
 
@@ -155,7 +163,7 @@ __global__ void init_kernel(StreamDev s) {
     for (int j = 0; j < s.K; ++j) {
       s.key[j * n + i] = wrs::kInf;
       s.idx[j * n + i] = wrs::kEmpty;
-      s.wt[j * n + i] = 0.0f;
+      if (s.wt) s.wt[j * n + i] = 0.0f;  // FP32 records are zeroed with the colour region
     }
   }
 }
@@ -170,15 +178,26 @@ __global__ void zero_kernel(uint8_t* p, int64_t bytes) {
 template <int KT, bool F16, int PX, bool VEC>
 __global__ void __launch_bounds__(256, PX == 4 ? 2 : 3) push_kernel(const __grid_constant__ StreamDev s,
                                                       const __grid_constant__ FrameDev f) {
+  __shared__ unsigned block_replaced;
+  if (threadIdx.x == 0) block_replaced = 0;
+  __syncthreads();
   const int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   const int64_t p0 = g * PX;
-  if (p0 >= s.hw) return;
-  const float d_f = wrs::fovea_density(s);
-  const wrs::Src src = wrs::global_src(s, f, static_cast<int>(p0), VEC);
-  if (f.fov != nullptr)
-    wrs::push_group<KT, F16, PX, VEC, true>(s, f, static_cast<int>(p0), src, d_f);
-  else
-    wrs::push_group<KT, F16, PX, VEC, false>(s, f, static_cast<int>(p0), src, d_f);
+  int replaced = 0;
+  if (p0 < s.hw) {
+    const float d_f = wrs::fovea_density(s);
+    const wrs::Src src = wrs::global_src(s, f, static_cast<int>(p0), VEC);
+    if (f.fov != nullptr)
+      replaced = wrs::push_group<KT, F16, PX, VEC, true>(s, f, static_cast<int>(p0), src, d_f);
+    else
+      replaced = wrs::push_group<KT, F16, PX, VEC, false>(s, f, static_cast<int>(p0), src, d_f);
+  }
+  // one atomic per block for the stream's replacement count
+  const unsigned c = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(replaced));
+  if ((threadIdx.x & 31) == 0 && c != 0) atomicAdd(&block_replaced, c);
+  __syncthreads();
+  if (threadIdx.x == 0 && block_replaced != 0)
+    atomicAdd(s.replacements, static_cast<unsigned long long>(block_replaced));
 }
 
 template <int KT, bool F16, int PX>
@@ -522,4 +541,17 @@ extern "C" int wrs_check_status(wrs_ctx* x, wrs_stream_t stream) {
                   "a device-side wait gave up after %llu ns; frames pushed since the last check "
                   "may be incomplete",
                   static_cast<unsigned long long>(x->timeout_ns));
+}
+
+extern "C" int wrs_get_stats(wrs_ctx* x, uint64_t* replacements, wrs_stream_t stream) {
+  clear_error();
+  if (!x || !replacements) return wrs_fail(WRS_ERR_ARG, "NULL argument");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned long long v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, x->state + x->lay.status_off + 8, sizeof v,
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_get_stats");
+  *replacements = v;
+  return WRS_OK;
 }

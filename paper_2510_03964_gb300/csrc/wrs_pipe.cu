@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kPipeThreads, PX == 1 ? 2 : 1)
   const int step = gridDim.x;
   const int my_tiles = first < a.ntiles ? (a.ntiles - 1 - first) / step + 1 : 0;
   int issued = 0;
+  int replaced = 0;
   if (warp == kConsumerWarps) {
     issued = wrs::produce(r, my_tiles, a.timeout_ns, lane,
                           [&](int it, uint8_t* st, float* u, uint64_t* full, int ln) {
@@ -78,10 +79,11 @@ __global__ void __launch_bounds__(kPipeThreads, PX == 1 ? 2 : 1)
     const float d_f = wrs::fovea_density(s);
     wrs::consume(r, my_tiles, a.timeout_ns, lane, [&](int it, const uint8_t* st, const float* u) {
       const int64_t p0 = static_cast<int64_t>(first + it * step) * T;
-      wrs::compute_tile<KT, F16, PX, T>(s, f, L, st, u, p0, d_f, tid);
+      replaced += wrs::compute_tile<KT, F16, PX, T>(s, f, L, st, u, p0, d_f, tid);
     });
   }
   __syncthreads();
+  if (warp < kConsumerWarps) wrs::add_warp_count(s.replacements, replaced, lane);
   if (wrs::flag_raised(r)) {
     if (warp == kConsumerWarps) wrs::drain(r, issued, a.timeout_ns);
     if (tid == 0) atomicExch(a.status, static_cast<uint32_t>(WRS_ERR_TIMEOUT));

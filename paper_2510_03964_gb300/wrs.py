@@ -141,6 +141,12 @@ class Stream:
         """Waits for the stream; returns 0, or the status code a device-side wait recorded."""
         return int(load().wrs_check_status(self._ctx, _stream_handle(stream)))
 
+    def replacements(self, stream=None) -> int:
+        """Slot replacements since create (waits for the stream)."""
+        v = C.c_uint64()
+        check(load().wrs_get_stats(self._ctx, C.byref(v), _stream_handle(stream)))
+        return int(v.value)
+
     def push_frame_host(self, h_frame: torch.Tensor, gaze, h_out: torch.Tensor, d_frame_stage,
                         d_out_stage, h_fov_map=None, d_fov_stage=None, stream=None):
         """Host frame in, host resolved frame out (copies inside the call)."""
@@ -176,15 +182,21 @@ def unpack_state(buf: np.ndarray, lay: WrsLayout, K: int, hw: int, color_fp16: b
     def plane(off, dtype, n):
         return np.frombuffer(buf, dtype=dtype, count=n * pl, offset=off).reshape(n, pl)[:, :hw]
 
-    cdt = np.float16 if color_fp16 else np.float32
-    return {
+    out = {
         "W": plane(lay.W_off, np.float32, 1)[0].copy(),
         "P": plane(lay.P_off, np.float32, 1)[0].copy(),
         "key": plane(lay.key_off, np.float32, K).copy(),
         "idx": plane(lay.idx_off, np.uint32, K).copy(),
-        "wt": plane(lay.wt_off, np.float32, K).copy(),
-        "col": plane(lay.col_off, cdt, 3 * K).reshape(3, K, hw).copy(),
     }
+    if color_fp16:
+        out["wt"] = plane(lay.wt_off, np.float32, K).copy()
+        out["col"] = plane(lay.col_off, np.float16, 3 * K).reshape(3, K, hw).copy()
+    else:
+        rec = np.frombuffer(buf, dtype=np.float32, count=K * pl * 4, offset=lay.col_off)
+        rec = rec.reshape(K, pl, 4)[:, :hw]
+        out["wt"] = rec[:, :, 0].copy()
+        out["col"] = np.ascontiguousarray(np.transpose(rec[:, :, 1:], (2, 0, 1)))
+    return out
 
 
 __all__ = ["Stream", "make_config", "state_bytes", "state_layout", "unpack_state", "WrsError",

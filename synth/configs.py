@@ -77,6 +77,10 @@ WORKLOADS = {
         "4k", "3840x2160 RGB, 240 frames, K=8, fovea 200 px, 2x to 500 px, 4x to 1000 px, 8x beyond, "
         "FP32 colour planes, same gaze model as hd",
         (StreamSpec(3840, 2160, 8, _RINGS_4K, seed=0, frames=240),)),
+    "hd_k8": Workload(
+        "hd_k8", "1920x1080 RGB FP32, 120 frames, K=8, fovea 120 px, rings as hd: the 4k slot "
+        "layout at a quarter of the pixels (profiling case)",
+        (StreamSpec(1920, 1080, 8, _RINGS_HD, seed=0, frames=120),)),
     "4k_fp16": Workload(
         "4k_fp16", "as 4k with FP16 colour planes (keys, weights and accumulation FP32)",
         (StreamSpec(3840, 2160, 8, _RINGS_4K, seed=0, frames=240, color_fp16=True),)),

@@ -36,13 +36,17 @@ def test_state_bytes_and_layout(lib):
     n = pkg.state_bytes(cfg)
     lay = pkg.state_layout(cfg)
     hw = 3840 * 2160
-    assert lay.plane_px % 64 == 0 and lay.plane_px >= hw
-    assert n == lay.total_bytes == 256 + lay.plane_px * 4 * (2 + 3 * 8) + lay.plane_px * 4 * 3 * 8
-    assert lay.status_off == 0
-    for off in (lay.W_off, lay.P_off, lay.key_off, lay.idx_off, lay.wt_off, lay.col_off):
+    pl = lay.plane_px
+    assert pl % 64 == 0 and pl >= hw
+    # FP32 colour: W, P, key[8], idx[8] float planes + 8 float4 {w, r, g, b} record planes
+    assert n == lay.total_bytes == 256 + pl * 4 * (2 + 2 * 8) + pl * 16 * 8
+    assert lay.status_off == 0 and lay.wt_off == -1 and lay.plane_bytes_col == 16 * pl
+    for off in (lay.W_off, lay.P_off, lay.key_off, lay.idx_off, lay.col_off):
         assert off % 256 == 0
     cfg16 = pkg.make_config(3840, 2160, 8, 200.0, color_fp16=True)
-    assert pkg.state_bytes(cfg16) == 256 + lay.plane_px * (4 * (2 + 3 * 8) + 2 * 3 * 8)
+    lay16 = pkg.state_layout(cfg16)
+    assert pkg.state_bytes(cfg16) == 256 + pl * (4 * (2 + 3 * 8) + 2 * 3 * 8)
+    assert lay16.wt_off > 0 and lay16.plane_bytes_col == 2 * pl
     # ragged size: planes padded to 64 entries
     lay2 = pkg.state_layout(pkg.make_config(37, 23, 3, 5.0))
     assert lay2.plane_px == 896

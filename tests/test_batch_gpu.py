@@ -79,6 +79,7 @@ def test_batch_equals_individual_pushes(launch):
     torch.cuda.synchronize()
     for i in range(len(MIX)):
         assert mixed[i].frame_index == solo[i].frame_index == frames
+        assert mixed[i].replacements() == solo[i].replacements() > 0
         assert_bits_equal(mixed[i].export_raw(), solo[i].export_raw(), f"stream {i} state")
         assert_bits_equal(outs_mix[i].cpu().numpy(), outs_solo[i].cpu().numpy(), f"stream {i} out")
     b.close()

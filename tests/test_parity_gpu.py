@@ -212,3 +212,26 @@ def test_oracle_philox_matches_curand_through_library_stream():
     g = run.gpu.export_state()
     u = oracle.uniforms(0xDEADBEEF12345678, 77, 0, 0, w * h)
     assert_bits_equal(g["key"][0], -oracle.log32(u), "keys = -ln u")
+
+
+@pytest.mark.parametrize("pipeline", [(True, 0, 0, 0), (False, 0, 0, 0)])
+@pytest.mark.parametrize("fp16", [False, True])
+def test_replacement_counter_matches_oracle(pipeline, fp16):
+    """The stream's replacement count equals the number of (pixel, frame)
+    pairs whose candidate entered a slot, counted from the oracle's states."""
+    run = PairedRun(96, 40, 4, r_f=10.0, frames=14, seed=21, jitter_px=20, color_fp16=fp16,
+                    pipeline=pipeline)
+    expected = 0
+    rng = np.random.default_rng(5)
+    for t in range(14):
+        before = run.orc.idx.copy()
+        fm = None
+        if t == 9:
+            fm = np.zeros((40, 96), np.uint8)
+            fm[rng.random((40, 96)) < 0.2] = 0xFF
+        run.step(t, fov_map=fm)
+        expected += int((run.orc.idx == t).any(axis=1).sum())
+        assert not np.any((run.orc.idx != before) & (run.orc.idx != t) & (run.orc.idx != oracle.EMPTY))
+    torch.cuda.synchronize()
+    run.compare()
+    assert run.gpu.replacements() == expected
