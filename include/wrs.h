@@ -83,8 +83,9 @@ typedef struct {
  *   FP32 colour: rec[j] float4 {w, r, g, b} at col_off + j*plane_bytes_col
  *                (plane_bytes_col = 16*plane_px; wt_off = -1). One record per
  *                slot keeps a replacement's writes in one 16-byte entry.
- *   FP16 colour: wt[j] float at wt_off + j*plane_bytes4 and col[c][j] half at
- *                col_off + (c*K + j)*plane_bytes_col (plane_bytes_col = 2*plane_px). */
+ *   FP16 colour: wt[j] float at wt_off + j*plane_bytes4 and rec[j], 8-byte records
+ *                {r, g, b, 0} of IEEE halves, at col_off + j*plane_bytes_col
+ *                (plane_bytes_col = 8*plane_px). */
 typedef struct {
   int64_t plane_px;
   int64_t plane_bytes4;     /* plane_px * 4 */

@@ -71,8 +71,9 @@ static __device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t pa
 }
 
 // Byte offsets of one stage's planes in shared memory (tile of T pixels).
-// cs = 2 (FP16 colour: weight plane + 3K half planes) or 4 (FP32 colour: K
-// float4 {w, r, g, b} record planes, starting at `col`; `wt` == `col`).
+// cs = 2 (FP16 colour: K weight planes, then K planes of 8-byte half records
+// {r, g, b, 0}) or 4 (FP32 colour: K float4 {w, r, g, b} record planes,
+// starting at `col`; `wt` == `col`).
 struct StageLayout {
   uint32_t frame, W, P, key, wt, col, bytes;
 };
@@ -86,7 +87,7 @@ __host__ __device__ __forceinline__ StageLayout stage_layout(int T, int K, int c
   if (cs == 2) {
     L.wt = L.key + 4u * K * T;
     L.col = L.wt + (resolve ? 4u * K * T : 0u);
-    L.bytes = L.col + (resolve ? 2u * 3u * K * T : 0u);
+    L.bytes = L.col + (resolve ? 8u * K * T : 0u);
   } else {
     L.wt = L.col = L.key + 4u * K * T;
     L.bytes = L.col + (resolve ? 16u * K * T : 0u);
@@ -107,10 +108,10 @@ __device__ __forceinline__ void issue_tile_copies(const StreamDev& s, const Fram
   const int64_t rem_plane = s.plane - p0, rem_px = s.hw - p0;
   const uint32_t n = static_cast<uint32_t>(rem_plane < T ? rem_plane : T);  // plane entries (x64)
   const uint32_t np = static_cast<uint32_t>(rem_px < T ? rem_px : T);       // pixels (x4)
-  const int ncopy = 3 + K + (resolve ? (cs == 2 ? 4 * K : K) : 0);
+  const int ncopy = 3 + K + (resolve ? (cs == 2 ? 2 * K : K) : 0);
   if (lane == 0) {
     uint32_t bytes = 12u * np + 8u * n + 4u * K * n;
-    if (resolve) bytes += cs == 2 ? (4u * K * n + 2u * 3u * K * n) : 16u * K * n;
+    if (resolve) bytes += cs == 2 ? (4u * K * n + 8u * K * n) : 16u * K * n;
     mbar_arrive_expect_tx(bar, bytes + extra_tx);
   }
   __syncwarp();
@@ -133,10 +134,9 @@ __device__ __forceinline__ void issue_tile_copies(const StreamDev& s, const Fram
       const int j = c - 3 - K;
       bulk_g2s(stage + L.wt + 4u * T * j, s.wt + j * pl + p0, 4u * n, bar);
     } else {
-      const int m = c - 3 - 2 * K;  // channel * K + slot
-      const uint8_t* src =
-          static_cast<const uint8_t*>(s.col) + static_cast<int64_t>(cs) * (m * pl + p0);
-      bulk_g2s(stage + L.col + static_cast<uint32_t>(cs) * T * m, src, cs * n, bar);
+      const int j = c - 3 - 2 * K;  // FP16 colour: record plane j
+      bulk_g2s(stage + L.col + 8u * T * j, static_cast<const uint2*>(s.col) + j * pl + p0,
+               8u * n, bar);
     }
   }
 }

@@ -139,8 +139,9 @@ struct StreamDev {
   float* key;        // [K][plane]
   uint32_t* idx;     // [K][plane]
   float* wt;         // FP16 colour: [K][plane] slot weights; FP32 colour: unused
-  void* col;         // FP16 colour: [3][K][plane] __half; FP32 colour: [K][plane] float4
-                     // records {w, r, g, b} (weight and colour of a slot in one 16-byte entry)
+  void* col;         // FP32 colour: [K][plane] float4 records {w, r, g, b} (weight and colour
+                     // of a slot in one 16-byte entry); FP16 colour: [K][plane] 8-byte
+                     // records {r, g, b, 0} of halves
   int64_t plane;     // entries per plane (multiple of 64)
   int32_t width, height, K, hw;
   uint32_t width_rcp; // ceil(2^32 / width) (0xFFFFFFFF for width 1): see row_of
@@ -245,17 +246,22 @@ __device__ __forceinline__ void store_col(void* base, int64_t off, float v) {
 
 // Weight and colour of slot j for a group of N pixels whose first entry is at
 // `at` in planes of `stride` entries. FP32 colour: one float4 record
-// {w, r, g, b} per entry in `col`; FP16 colour: a weight plane and 3K half
-// planes.
+// {w, r, g, b} per entry in `col`; FP16 colour: a weight plane and an 8-byte
+// record {r, g, b, 0} of halves per entry in `col`.
 template <bool F16, int N>
 __device__ __forceinline__ void load_slot(const float* wt, const void* col, int K, int j,
                                           int64_t stride, int64_t at, float (&a)[N],
                                           float (&r)[N], float (&g)[N], float (&b)[N]) {
   if constexpr (F16) {
     load_f<N>(wt + j * stride + at, a);
-    load_h<N>(static_cast<const __half*>(col) + (0 * K + j) * stride + at, r);
-    load_h<N>(static_cast<const __half*>(col) + (1 * K + j) * stride + at, g);
-    load_h<N>(static_cast<const __half*>(col) + (2 * K + j) * stride + at, b);
+    const uint2* rec = static_cast<const uint2*>(col) + j * stride + at;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const uint2 v = rec[i];
+      r[i] = __half2float(__ushort_as_half(static_cast<unsigned short>(v.x & 0xffffu)));
+      g[i] = __half2float(__ushort_as_half(static_cast<unsigned short>(v.x >> 16)));
+      b[i] = __half2float(__ushort_as_half(static_cast<unsigned short>(v.y & 0xffffu)));
+    }
   } else {
     const float4* rec = static_cast<const float4*>(col) + j * stride + at;
 #pragma unroll
@@ -275,9 +281,10 @@ __device__ __forceinline__ void store_slot(float* wt, void* col, int K, int j, i
                                            int64_t p, float w, float r, float g, float b) {
   if constexpr (F16) {
     wt[j * plane + p] = w;
-    store_col<true>(col, (0 * K + j) * plane + p, r);
-    store_col<true>(col, (1 * K + j) * plane + p, g);
-    store_col<true>(col, (2 * K + j) * plane + p, b);
+    const uint32_t rb = __half_as_ushort(__float2half_rn(r));
+    const uint32_t gb = __half_as_ushort(__float2half_rn(g));
+    const uint32_t bb = __half_as_ushort(__float2half_rn(b));
+    static_cast<uint2*>(col)[j * plane + p] = make_uint2(rb | (gb << 16), bb);
   } else {
     static_cast<float4*>(col)[j * plane + p] = make_float4(w, r, g, b);
   }

@@ -70,7 +70,7 @@ void wrs_make_layout(const wrs_config* c, wrs_layout* L) {
   const int64_t pl = (hw + kPlaneAlign - 1) / kPlaneAlign * kPlaneAlign;
   L->plane_px = pl;
   L->plane_bytes4 = pl * 4;
-  L->plane_bytes_col = pl * (c->color_fp16 ? 2 : 16);
+  L->plane_bytes_col = pl * (c->color_fp16 ? 8 : 16);
   L->status_off = 0;
   L->W_off = kStatusBytes;
   L->P_off = L->W_off + L->plane_bytes4;
@@ -79,7 +79,7 @@ void wrs_make_layout(const wrs_config* c, wrs_layout* L) {
   if (c->color_fp16) {
     L->wt_off = L->idx_off + c->K * L->plane_bytes4;
     L->col_off = L->wt_off + c->K * L->plane_bytes4;
-    L->total_bytes = L->col_off + 3 * c->K * L->plane_bytes_col;
+    L->total_bytes = L->col_off + c->K * L->plane_bytes_col;
   } else {
     // FP32 colour: weight and colour of a slot in one float4 record
     L->wt_off = -1;

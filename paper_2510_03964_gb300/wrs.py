@@ -190,7 +190,9 @@ def unpack_state(buf: np.ndarray, lay: WrsLayout, K: int, hw: int, color_fp16: b
     }
     if color_fp16:
         out["wt"] = plane(lay.wt_off, np.float32, K).copy()
-        out["col"] = plane(lay.col_off, np.float16, 3 * K).reshape(3, K, hw).copy()
+        rec = np.frombuffer(buf, dtype=np.float16, count=K * pl * 4, offset=lay.col_off)
+        rec = rec.reshape(K, pl, 4)[:, :hw]
+        out["col"] = np.ascontiguousarray(np.transpose(rec[:, :, :3], (2, 0, 1)))
     else:
         rec = np.frombuffer(buf, dtype=np.float32, count=K * pl * 4, offset=lay.col_off)
         rec = rec.reshape(K, pl, 4)[:, :hw]

@@ -45,8 +45,9 @@ def test_state_bytes_and_layout(lib):
         assert off % 256 == 0
     cfg16 = pkg.make_config(3840, 2160, 8, 200.0, color_fp16=True)
     lay16 = pkg.state_layout(cfg16)
-    assert pkg.state_bytes(cfg16) == 256 + pl * (4 * (2 + 3 * 8) + 2 * 3 * 8)
-    assert lay16.wt_off > 0 and lay16.plane_bytes_col == 2 * pl
+    # FP16 colour: W, P, key[8], idx[8], wt[8] float planes + 8 records of 4 halves
+    assert pkg.state_bytes(cfg16) == 256 + pl * (4 * (2 + 3 * 8) + 8 * 8)
+    assert lay16.wt_off > 0 and lay16.plane_bytes_col == 8 * pl
     # ragged size: planes padded to 64 entries
     lay2 = pkg.state_layout(pkg.make_config(37, 23, 3, 5.0))
     assert lay2.plane_px == 896
