@@ -238,6 +238,86 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, dev):
+    """The 16-stream uneven-resolution workload: one persistent batched launch per
+    round (autotuned tile/stages/CTAs, CUDA graph) vs 16 single-stream launches."""
+    import paper_2510_03964_gb300 as wrs
+    from paper_2510_03964_gb300 import autotune
+    wl = workload("mix16")
+    specs = wl.streams
+    nfr = 4
+    frames, gazes = [], []
+    for s in specs:
+        fv = Foveator(s.width, s.height, s.radii, seed=s.seed, device=dev)
+        gz = gaze_path(s.width, s.height, nfr, seed=s.seed)
+        fr = torch.empty((nfr, s.height, s.width, 3), dtype=torch.float32, device=dev)
+        for t in range(nfr):
+            fv.frame(float(gz[t, 0]), float(gz[t, 1]), out=fr[t])
+        frames.append(fr)
+        gazes.append(gz)
+    outs = [torch.empty((s.height, s.width, 3), dtype=torch.float32, device=dev) for s in specs]
+    tuned = autotune.tune_batch([(s.width, s.height, s.K, s.color_fp16, s.r_f) for s in specs], device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def make():
+        return [wrs.Stream(s.width, s.height, s.K, s.r_f, seed=s.seed, stream_id=s.stream_id,
+                           color_fp16=s.color_fp16, device=dev, stream=stream) for s in specs]
+
+    def timed(fn, rounds):
+        for r in range(3):
+            fn(r)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for r in range(rounds):
+            fn(3 + r)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / rounds
+
+    sts = make()
+    batch = wrs.Batch(len(specs))
+    batch.set_launch(*tuned["batch"])
+    r0 = sum(x.replacements(stream=stream) for x in sts)
+
+    def batched_round(t):
+        batch.push(sts, [f[t % nfr] for f in frames], [g[t % nfr] for g in gazes], outs=outs, stream=stream)
+
+    ms_batch = timed(batched_round, args.batch_rounds)
+    rho = (sum(x.replacements(stream=stream) for x in sts) - r0) / float(wl.pixels * (args.batch_rounds + 3))
+    for x in sts:
+        x.close()
+    sts2 = make()
+
+    def solo_round(t):
+        for i, x in enumerate(sts2):
+            x.push_frame(frames[i][t % nfr], gazes[i][t % nfr], None, outs[i], stream=stream)
+
+    ms_solo = timed(solo_round, args.batch_rounds)
+    for x in sts2:
+        x.close()
+    batch.close()
+    peaks = measured_peaks()
+    bytes_round = sum(s.pixels * (algorithmic_bytes_per_px(s.K, s.color_fp16) + rho * replacement_bytes(s.color_fp16))
+                      for s in specs)
+    achieved = bytes_round / (ms_batch * 1e-3) / 1e9
+    del frames, outs
+    return {"workload": wl.description, "pixels_per_round": wl.pixels, "rounds": args.batch_rounds,
+            "ms_per_round_batched": round(ms_batch, 4), "ms_per_round_16_launches": round(ms_solo, 4),
+            "mpx_updates_per_s": round(wl.pixels / (ms_batch * 1e-3) / 1e6, 1),
+            "replacement_rate": round(rho, 4),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4)},
+            "launch": {"px_per_thread": tuned["batch"][0], "stages": tuned["batch"][1],
+                       "ctas_per_sm": tuned["batch"][2], "graph": tuned["batch"][3],
+                       "tile_px": 256 * tuned["batch"][0], "chosen_by": "autotune.tune_batch"}}
+
+
+def run_serving(args, dev):
+    from paper_2510_03964_gb300 import serve
+    return serve.serve_compare(n_viewers=64, duration_s=args.serve, budget_gb=60.0, seed=0, device=dev)
+
+
 def workload_config(spec, name):
     return {"workload": f"{name}: {spec.width}x{spec.height} RGB, K={spec.K}, "
                         f"{'FP16' if spec.color_fp16 else 'FP32'} colour planes, fovea {spec.r_f:g} px, "
@@ -337,15 +417,23 @@ def run_ours(args, world, rank, local):
     if rank != 0:
         st.close()
         return
+    st_pipe = st.get_pipeline()
+    st_launch = st.get_launch()
+    del frames
+    torch.cuda.empty_cache()
+    batched = run_batched(args, dev) if args.batch_rounds > 0 else None
+    torch.cuda.empty_cache()
+    serving = run_serving(args, dev) if args.serve > 0 else None
+    torch.cuda.empty_cache()
 
     peaks = measured_peaks()
     bpp = algorithmic_bytes_per_px(spec.K, spec.color_fp16) + rho * replacement_bytes(spec.color_fp16)
     achieved = bpp * hw / (kernel_avg * 1e-3) / 1e9
-    kname = (f"{'pipe_kernel' if st.get_pipeline()[0] else 'push_kernel'}"
+    kname = (f"{'pipe_kernel' if st_pipe[0] else 'push_kernel'}"
              f"<K={spec.K},{'fp16' if spec.color_fp16 else 'fp32'}>")
     cfg = workload_config(spec, args.workload)
-    pipe_on, pipe_px, pipe_st, pipe_ctas = st.get_pipeline()
-    blk, px = st.get_launch()
+    pipe_on, pipe_px, pipe_st, pipe_ctas = st_pipe
+    blk, px = st_launch
     cfg["kernel"] = (f"pipelined: {pipe_px} px/thread, tile {256 * pipe_px} px, {pipe_st} stages, "
                      f"{pipe_ctas or 'max'} CTAs/SM"
                      if pipe_on else f"plain: block {blk}, {px} px/thread")
@@ -373,6 +461,8 @@ def run_ours(args, world, rank, local):
         "gpu_launches": args.steps,
         "clocks": clk,
         "e2e": e2e,
+        "batched": batched,
+        "serving": serving,
     }
     if args.cpu_baseline:
         nthreads = os.cpu_count() or 1
@@ -407,6 +497,10 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=131072)
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--ref-sample", type=int, default=65536)
+    ap.add_argument("--batch-rounds", type=int, default=100,
+                    help="rounds of the 16-stream batched workload (0 skips it)")
+    ap.add_argument("--serve", type=float, default=10.0,
+                    help="seconds of the 64-viewer serving trace per mode (0 skips it)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -1,0 +1,358 @@
+"""Serving many viewers' foveated frame streams on one GPU.
+
+Viewers join and leave over time; each sends frames as a Poisson process.
+Every admitted viewer's reservoirs stay resident in HBM, and viewers are
+admitted while their reservoir bytes fit under an HBM budget (the rest wait
+in a FIFO queue and are admitted as others leave; frames a viewer sends before
+admission are rejected).
+
+Two dispatch modes run the same arrival trace:
+
+* ``batched`` (continuous batching): whenever fewer than ``max_inflight``
+  launches are on the GPU, every viewer with a pending frame and no frame in
+  flight contributes its oldest pending frame to one persistent batched
+  launch (wrs_push_batch, a CUDA-graph kernel node); frames that arrive while
+  launches run join the next one. Launches alternate between CUDA streams, so
+  consecutive batches overlap on the device.
+* ``plain``: every frame is launched on its own (wrs_push_frame) as soon as it
+  arrives, on one stream.
+
+A frame's latency is the time from its arrival to the host observing its
+launch's completion event. Results per frame are identical in both modes and
+to a viewer served alone (each viewer's frames are applied in arrival order).
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import statistics
+import time
+
+import numpy as np
+import torch
+
+from .wrs import Batch, Stream, make_config, state_bytes
+
+# resolution classes of the mixed-viewer workload: (width, height, ring radii)
+CLASSES = ((3840, 2160, (200.0, 500.0, 1000.0)), (2064, 2208, (200.0, 500.0, 1000.0)),
+           (1440, 1600, (150.0, 375.0, 750.0)), (1920, 1080, (120.0, 300.0)))
+
+
+@dataclasses.dataclass
+class ViewerSpec:
+    vid: int
+    width: int
+    height: int
+    K: int
+    radii: tuple
+    seed: int
+    rate_hz: float
+    join_s: float
+    leave_s: float
+    cls: int
+    color_fp16: bool = True
+
+    @property
+    def pixels(self) -> int:
+        return self.width * self.height
+
+    def state_bytes(self) -> int:
+        return state_bytes(make_config(self.width, self.height, self.K, self.radii[0],
+                                       color_fp16=self.color_fp16))
+
+
+def viewer_mix(n: int = 64, duration_s: float = 60.0, seed: int = 0,
+               rate_hz=(72.0, 120.0), classes=CLASSES) -> list[ViewerSpec]:
+    """n viewers cycling through the resolution classes, K = 8 for even and 4
+    for odd viewer index, frame rates uniform in rate_hz, joining within the
+    first half of the run and staying 30-90% of it."""
+    g = np.random.Generator(np.random.Philox(key=[seed, 11]))
+    out = []
+    for i in range(n):
+        w, h, radii = classes[i % len(classes)]
+        join = float(g.random() * 0.5 * duration_s)
+        stay = float((0.3 + 0.6 * g.random()) * duration_s)
+        out.append(ViewerSpec(vid=i, width=w, height=h, K=8 if i % 2 == 0 else 4, radii=radii,
+                              seed=i + 1, rate_hz=float(rate_hz[0] + g.random() * (rate_hz[1] - rate_hz[0])),
+                              join_s=join, leave_s=min(duration_s, join + stay), cls=i % len(classes)))
+    return out
+
+
+def arrivals(specs, seed: int = 0):
+    """Sorted (time_s, vid) of every frame each viewer sends between join and leave."""
+    g = np.random.Generator(np.random.Philox(key=[seed, 12]))
+    ev = []
+    for v in specs:
+        t = v.join_s
+        while True:
+            t += float(g.exponential(1.0 / v.rate_hz))
+            if t >= v.leave_s:
+                break
+            ev.append((t, v.vid))
+    ev.sort()
+    return ev
+
+
+class FramePool:
+    """A few pre-generated foveated frames per resolution class, resident on the
+    device; viewer frame t uses frame t mod F of its class with its gaze."""
+
+    def __init__(self, classes, frames_per_class: int, device, seed: int = 0):
+        from synth import Foveator, gaze_path  # input generator, not part of the method
+        self.frames, self.gaze = [], []
+        for ci, (w, h, radii) in enumerate(classes):
+            fv = Foveator(w, h, radii, seed=seed + ci, device=device)
+            gz = gaze_path(w, h, frames_per_class, seed=seed + ci)
+            fr = torch.empty((frames_per_class, h, w, 3), dtype=torch.float32, device=device)
+            for t in range(frames_per_class):
+                fv.frame(float(gz[t, 0]), float(gz[t, 1]), out=fr[t])
+            self.frames.append(fr)
+            self.gaze.append(gz)
+        self.F = frames_per_class
+
+    def get(self, cls: int, t: int):
+        i = t % self.F
+        return self.frames[cls][i], self.gaze[cls][i]
+
+
+@dataclasses.dataclass
+class ServeStats:
+    mode: str
+    duration_s: float
+    frames_served: int
+    frames_rejected: int
+    pixel_updates: int
+    latencies_ms: list
+    launches: int
+    viewers_admitted: int
+    viewers_queued_max: int
+    peak_state_bytes: int
+
+    def summary(self) -> dict:
+        lat = sorted(self.latencies_ms)
+
+        def pct(q):
+            if not lat:
+                return None
+            return round(lat[min(len(lat) - 1, int(q * len(lat)))], 3)
+
+        return {"mode": self.mode, "duration_s": round(self.duration_s, 2),
+                "frames_served": self.frames_served, "frames_rejected": self.frames_rejected,
+                "p50_ms": pct(0.50), "p99_ms": pct(0.99),
+                "mean_ms": round(statistics.mean(lat), 3) if lat else None,
+                "mpx_updates_per_s": round(self.pixel_updates / self.duration_s / 1e6, 1),
+                "launches": self.launches, "frames_per_launch": round(self.frames_served / max(1, self.launches), 2),
+                "viewers_admitted": self.viewers_admitted, "viewers_queued_max": self.viewers_queued_max,
+                "peak_state_gb": round(self.peak_state_bytes / 1e9, 2)}
+
+
+class Server:
+    """Runs one arrival trace in real time in one of the two dispatch modes."""
+
+    def __init__(self, specs, pool: FramePool, budget_bytes: int, mode: str = "batched",
+                 max_inflight: int = 2, device=None, keep_states: bool = False,
+                 batch_launch=None):
+        assert mode in ("batched", "plain")
+        self.specs = {v.vid: v for v in specs}
+        self.pool = pool
+        self.budget = int(budget_bytes)
+        self.mode = mode
+        self.max_inflight = max_inflight
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        self.keep_states = keep_states
+        n_streams = max_inflight if mode == "batched" else 1
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(n_streams)]
+        self.batch = Batch(min(64, max(1, len(specs)))) if mode == "batched" else None
+        if self.batch is not None and batch_launch:
+            self.batch.set_launch(*batch_launch)
+        self.init_stream = torch.cuda.Stream(device=self.device)
+        self.init_ev = {}         # vid -> event after its state initialisation
+        self.used = 0
+        self.live = {}            # vid -> Stream
+        self.pushed = collections.defaultdict(list)  # vid -> frame counters pushed, in order
+        self.kept = {}            # vid -> Stream kept after leaving (keep_states)
+
+    # -- admission ---------------------------------------------------------
+    def _admit(self, vid) -> bool:
+        v = self.specs[vid]
+        need = v.state_bytes()
+        if self.used + need > self.budget:
+            return False
+        st = Stream(v.width, v.height, v.K, v.radii[0], seed=v.seed, stream_id=vid,
+                    color_fp16=v.color_fp16, device=self.device, stream=self.init_stream)
+        ev = torch.cuda.Event()
+        ev.record(self.init_stream)
+        self.init_ev[vid] = ev
+        self.live[vid] = st
+        self.used += need
+        return True
+
+    def _ready(self, vid, stream):
+        # a launch that touches a newly admitted viewer waits for its initialisation
+        ev = self.init_ev.pop(vid, None)
+        if ev is not None:
+            stream.wait_event(ev)
+
+    def _release(self, vid):
+        self.init_ev.pop(vid, None)
+        st = self.live.pop(vid)
+        self.used -= self.specs[vid].state_bytes()
+        if self.keep_states:
+            self.kept[vid] = st
+        else:
+            st.close()
+            del st
+
+    def run(self, trace, duration_s: float) -> ServeStats:
+        dev = self.device
+        torch.cuda.synchronize(dev)
+        joins = sorted((v.join_s, vid) for vid, v in self.specs.items())
+        leaves = sorted((v.leave_s, vid) for vid, v in self.specs.items())
+        ji = li = ai = 0
+        waitq = collections.deque()
+        pending = collections.defaultdict(collections.deque)  # vid -> deque of arrival times
+        next_t = collections.defaultdict(int)                 # vid -> next frame counter
+        busy = collections.Counter()  # vid -> frames in flight
+        leaving = set()
+        inflight = []         # (event, [(vid, arrival_s)])
+        lat, served, rejected, pix, launches = [], 0, 0, 0, 0
+        admitted_total, queued_max, peak = 0, 0, 0
+        slot = 0
+        t0 = time.perf_counter()
+        while True:
+            now = time.perf_counter() - t0
+            # joins
+            while ji < len(joins) and joins[ji][0] <= now:
+                vid = joins[ji][1]
+                ji += 1
+                if self._admit(vid):
+                    admitted_total += 1
+                else:
+                    waitq.append(vid)
+                queued_max = max(queued_max, len(waitq))
+            # leaves: release once nothing of the viewer is pending or in flight
+            while li < len(leaves) and leaves[li][0] <= now:
+                leaving.add(leaves[li][1])
+                li += 1
+            for vid in list(leaving):
+                if vid in waitq:
+                    waitq.remove(vid)
+                    leaving.discard(vid)
+                elif vid in self.live and busy[vid] == 0 and not pending[vid]:
+                    self._release(vid)
+                    leaving.discard(vid)
+                elif vid not in self.live and vid not in waitq:
+                    leaving.discard(vid)
+            while waitq and self._admit(waitq[0]):
+                waitq.popleft()
+                admitted_total += 1
+            peak = max(peak, self.used)
+            # arrivals
+            while ai < len(trace) and trace[ai][0] <= min(now, duration_s):
+                ta, vid = trace[ai]
+                ai += 1
+                if vid in self.live and vid not in leaving:
+                    pending[vid].append(ta)
+                else:
+                    rejected += 1
+            # completions
+            still = []
+            done_now = time.perf_counter() - t0
+            for ev, frames in inflight:
+                if ev.query():
+                    for vid, ta in frames:
+                        lat.append((done_now - ta) * 1e3)
+                        busy[vid] -= 1
+                        served += 1
+                        pix += self.specs[vid].pixels
+                else:
+                    still.append((ev, frames))
+            inflight = still
+            # dispatch
+            if self.mode == "batched":
+                if len(inflight) < self.max_inflight:
+                    ready = [vid for vid in self.live if pending[vid] and busy[vid] == 0]
+                    ready = ready[:self.batch.max_streams]
+                    if ready:
+                        stream = self.streams[slot % len(self.streams)]
+                        slot += 1
+                        sts, frs, gzs, frames = [], [], [], []
+                        for vid in ready:
+                            ta = pending[vid].popleft()
+                            t = next_t[vid]
+                            next_t[vid] += 1
+                            fr, gz = self.pool.get(self.specs[vid].cls, t)
+                            sts.append(self.live[vid])
+                            frs.append(fr)
+                            gzs.append(gz)
+                            frames.append((vid, ta))
+                            busy[vid] += 1
+                            self._ready(vid, stream)
+                            self.pushed[vid].append(t)
+                        self.batch.push(sts, frs, gzs, stream=stream)
+                        ev = torch.cuda.Event()
+                        ev.record(stream)
+                        inflight.append((ev, frames))
+                        launches += 1
+            else:
+                stream = self.streams[0]
+                for vid in list(self.live):
+                    while pending[vid]:
+                        ta = pending[vid].popleft()
+                        t = next_t[vid]
+                        next_t[vid] += 1
+                        fr, gz = self.pool.get(self.specs[vid].cls, t)
+                        self._ready(vid, stream)
+                        self.live[vid].push_frame(fr, gz, stream=stream)
+                        busy[vid] += 1
+                        ev = torch.cuda.Event()
+                        ev.record(stream)
+                        inflight.append((ev, [(vid, ta)]))
+                        self.pushed[vid].append(t)
+                        launches += 1
+            if now >= duration_s and not inflight and all(not q for q in pending.values()):
+                break
+            if not inflight and ai < len(trace) and trace[ai][0] > now + 0.0005:
+                time.sleep(min(0.0005, trace[ai][0] - now))
+        torch.cuda.synchronize(dev)
+        elapsed = time.perf_counter() - t0
+        for vid in list(self.live):
+            self._release(vid)
+        return ServeStats(self.mode, max(elapsed, duration_s), served, rejected, pix, lat, launches,
+                          admitted_total, queued_max, peak)
+
+    def close(self):
+        if self.batch is not None:
+            self.batch.close()
+        for st in list(self.live.values()) + list(self.kept.values()):
+            st.close()
+        self.live.clear()
+        self.kept.clear()
+
+
+def replay_alone(spec: ViewerSpec, pushed, pool: FramePool, device=None) -> Stream:
+    """The viewer's frames pushed alone, in the same order, one launch each."""
+    st = Stream(spec.width, spec.height, spec.K, spec.radii[0], seed=spec.seed, stream_id=spec.vid,
+                color_fp16=spec.color_fp16, device=device)
+    for t in pushed:
+        fr, gz = pool.get(spec.cls, t)
+        st.push_frame(fr, gz)
+    return st
+
+
+def serve_compare(n_viewers=64, duration_s=10.0, budget_gb=60.0, seed=0, frames_per_class=8,
+                  device=None, rate_hz=(72.0, 120.0), batch_launch=None, classes=CLASSES) -> dict:
+    """Both modes on the same trace; returns their summaries."""
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    specs = viewer_mix(n_viewers, duration_s, seed, rate_hz, classes)
+    trace = arrivals(specs, seed)
+    pool = FramePool(classes, frames_per_class, dev, seed)
+    out = {"viewers": n_viewers, "duration_s": duration_s, "budget_gb": budget_gb,
+           "frames_offered": len(trace)}
+    for mode in ("batched", "plain"):
+        srv = Server(specs, pool, int(budget_gb * 1e9), mode=mode, device=dev,
+                     batch_launch=batch_launch)
+        out[mode] = srv.run(trace, duration_s).summary()
+        srv.close()
+        torch.cuda.synchronize(dev)
+    return out
