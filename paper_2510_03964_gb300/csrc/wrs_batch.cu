@@ -151,6 +151,7 @@ struct wrs_batch {
   cudaGraphNode_t node[3];
   size_t configured_smem[3];
   int device;
+  int rebuilds;  // graph nodes rebuilt because an in-place update was refused
 };
 
 static int px_slot(int px) { return px == 4 ? 2 : (px == 2 ? 1 : 0); }
@@ -298,10 +299,13 @@ extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
     }
     b->device = device;
   }
-  if (smem > b->configured_smem[slot]) {
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (b->configured_smem[slot] == 0) {
+    // allow the whole budget once, before any graph is built: a graph keeps the
+    // limit it was instantiated under, and later batches may need larger stages
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmemBudget));
     if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_batch: shared memory attribute");
-    b->configured_smem[slot] = smem;
+    b->configured_smem[slot] = kSmemBudget;
   }
   int fit = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, kBatchThreads, smem);
@@ -321,14 +325,23 @@ extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
   kp.kernelParams = params;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (b->use_graph) {
+    if (b->exec[slot]) {
+      e = cudaGraphExecKernelNodeSetParams(b->exec[slot], b->node[slot], &kp);
+      if (e != cudaSuccess) {
+        // the in-place update was refused: rebuild the node below
+        (void)cudaGetLastError();
+        cudaGraphExecDestroy(b->exec[slot]);
+        cudaGraphDestroy(b->graph[slot]);
+        b->exec[slot] = nullptr;
+        b->graph[slot] = nullptr;
+        b->rebuilds += 1;
+      }
+    }
     if (!b->exec[slot]) {
       e = cudaGraphCreate(&b->graph[slot], 0);
       if (e == cudaSuccess) e = cudaGraphAddKernelNode(&b->node[slot], b->graph[slot], nullptr, 0, &kp);
       if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[slot], b->graph[slot], 0);
       if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_batch: graph build");
-    } else {
-      e = cudaGraphExecKernelNodeSetParams(b->exec[slot], b->node[slot], &kp);
-      if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_batch: graph update");
     }
     e = cudaGraphLaunch(b->exec[slot], st);
     if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_batch: graph launch");

@@ -8,12 +8,13 @@ admission are rejected).
 
 Two dispatch modes run the same arrival trace:
 
-* ``batched`` (continuous batching): whenever fewer than ``max_inflight``
-  launches are on the GPU, every viewer with a pending frame and no frame in
-  flight contributes its oldest pending frame to one persistent batched
-  launch (wrs_push_batch, a CUDA-graph kernel node); frames that arrive while
-  launches run join the next one. Launches alternate between CUDA streams, so
-  consecutive batches overlap on the device.
+* ``batched`` (continuous batching): every viewer is pinned to one of
+  ``n_streams`` CUDA streams, so stream order keeps its frames in sequence.
+  Whenever a stream has fewer than ``depth`` launches queued, each of its
+  viewers with a pending frame contributes its oldest one to one persistent
+  batched launch (wrs_push_batch, a CUDA-graph kernel node); frames that
+  arrive while launches run join the next one. Batches on different streams
+  overlap on the device.
 * ``plain``: every frame is launched on its own (wrs_push_frame) as soon as it
   arrives, on one stream.
 
@@ -150,21 +151,27 @@ class Server:
     """Runs one arrival trace in real time in one of the two dispatch modes."""
 
     def __init__(self, specs, pool: FramePool, budget_bytes: int, mode: str = "batched",
-                 max_inflight: int = 2, device=None, keep_states: bool = False,
+                 n_streams: int = 2, depth: int = 2, device=None, keep_states: bool = False,
                  batch_launch=None):
         assert mode in ("batched", "plain")
         self.specs = {v.vid: v for v in specs}
         self.pool = pool
         self.budget = int(budget_bytes)
         self.mode = mode
-        self.max_inflight = max_inflight
+        self.depth = depth
         self.device = torch.device("cuda") if device is None else torch.device(device)
         self.keep_states = keep_states
-        n_streams = max_inflight if mode == "batched" else 1
+        n_streams = n_streams if mode == "batched" else 1
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(n_streams)]
-        self.batch = Batch(min(64, max(1, len(specs)))) if mode == "batched" else None
-        if self.batch is not None and batch_launch:
-            self.batch.set_launch(*batch_launch)
+        # one launcher per stream: a launcher's graph is updated in place, so
+        # two launches queued on different streams must not share one
+        self.batches = []
+        if mode == "batched":
+            for _ in range(n_streams):
+                b = Batch(min(64, max(1, len(specs))))
+                if batch_launch:
+                    b.set_launch(*batch_launch)
+                self.batches.append(b)
         self.init_stream = torch.cuda.Stream(device=self.device)
         self.init_ev = {}         # vid -> event after its state initialisation
         self.used = 0
@@ -214,10 +221,10 @@ class Server:
         next_t = collections.defaultdict(int)                 # vid -> next frame counter
         busy = collections.Counter()  # vid -> frames in flight
         leaving = set()
-        inflight = []         # (event, [(vid, arrival_s)])
+        inflight = []         # (event, stream index, [(vid, arrival_s)])
+        queued = collections.Counter()  # stream index -> launches in flight
         lat, served, rejected, pix, launches = [], 0, 0, 0, 0
         admitted_total, queued_max, peak = 0, 0, 0
-        slot = 0
         t0 = time.perf_counter()
         while True:
             now = time.perf_counter() - t0
@@ -258,42 +265,46 @@ class Server:
             # completions
             still = []
             done_now = time.perf_counter() - t0
-            for ev, frames in inflight:
+            for ev, si, frames in inflight:
                 if ev.query():
+                    queued[si] -= 1
                     for vid, ta in frames:
                         lat.append((done_now - ta) * 1e3)
                         busy[vid] -= 1
                         served += 1
                         pix += self.specs[vid].pixels
                 else:
-                    still.append((ev, frames))
+                    still.append((ev, si, frames))
             inflight = still
             # dispatch
             if self.mode == "batched":
-                if len(inflight) < self.max_inflight:
-                    ready = [vid for vid in self.live if pending[vid] and busy[vid] == 0]
-                    ready = ready[:self.batch.max_streams]
-                    if ready:
-                        stream = self.streams[slot % len(self.streams)]
-                        slot += 1
-                        sts, frs, gzs, frames = [], [], [], []
-                        for vid in ready:
-                            ta = pending[vid].popleft()
-                            t = next_t[vid]
-                            next_t[vid] += 1
-                            fr, gz = self.pool.get(self.specs[vid].cls, t)
-                            sts.append(self.live[vid])
-                            frs.append(fr)
-                            gzs.append(gz)
-                            frames.append((vid, ta))
-                            busy[vid] += 1
-                            self._ready(vid, stream)
-                            self.pushed[vid].append(t)
-                        self.batch.push(sts, frs, gzs, stream=stream)
-                        ev = torch.cuda.Event()
-                        ev.record(stream)
-                        inflight.append((ev, frames))
-                        launches += 1
+                for si, stream in enumerate(self.streams):
+                    if queued[si] >= self.depth:
+                        continue
+                    ready = [vid for vid in self.live
+                             if vid % len(self.streams) == si and pending[vid]]
+                    ready = ready[:self.batches[si].max_streams]
+                    if not ready:
+                        continue
+                    sts, frs, gzs, frames = [], [], [], []
+                    for vid in ready:
+                        ta = pending[vid].popleft()
+                        t = next_t[vid]
+                        next_t[vid] += 1
+                        fr, gz = self.pool.get(self.specs[vid].cls, t)
+                        sts.append(self.live[vid])
+                        frs.append(fr)
+                        gzs.append(gz)
+                        frames.append((vid, ta))
+                        busy[vid] += 1
+                        self._ready(vid, stream)
+                        self.pushed[vid].append(t)
+                    self.batches[si].push(sts, frs, gzs, stream=stream)
+                    ev = torch.cuda.Event()
+                    ev.record(stream)
+                    inflight.append((ev, si, frames))
+                    queued[si] += 1
+                    launches += 1
             else:
                 stream = self.streams[0]
                 for vid in list(self.live):
@@ -307,7 +318,7 @@ class Server:
                         busy[vid] += 1
                         ev = torch.cuda.Event()
                         ev.record(stream)
-                        inflight.append((ev, [(vid, ta)]))
+                        inflight.append((ev, 0, [(vid, ta)]))
                         self.pushed[vid].append(t)
                         launches += 1
             if now >= duration_s and not inflight and all(not q for q in pending.values()):
@@ -322,8 +333,8 @@ class Server:
                           admitted_total, queued_max, peak)
 
     def close(self):
-        if self.batch is not None:
-            self.batch.close()
+        for b in self.batches:
+            b.close()
         for st in list(self.live.values()) + list(self.kept.values()):
             st.close()
         self.live.clear()
