@@ -314,8 +314,15 @@ def run_batched(args, dev):
 
 
 def run_serving(args, dev):
+    """The 64-viewer serving trace at the workload's frame rates (72-120 Hz per
+    viewer) and at an overload (200-300 Hz), batched vs one launch per frame."""
     from paper_2510_03964_gb300 import serve
-    return serve.serve_compare(n_viewers=64, duration_s=args.serve, budget_gb=60.0, seed=0, device=dev)
+    out = {}
+    for name, rate in (("rates_72_120hz", (72.0, 120.0)), ("overload_200_300hz", (200.0, 300.0))):
+        out[name] = serve.serve_compare(n_viewers=64, duration_s=args.serve, budget_gb=60.0, seed=0,
+                                        device=dev, rate_hz=rate)
+        torch.cuda.empty_cache()
+    return out
 
 
 def workload_config(spec, name):
@@ -499,8 +506,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=65536)
     ap.add_argument("--batch-rounds", type=int, default=100,
                     help="rounds of the 16-stream batched workload (0 skips it)")
-    ap.add_argument("--serve", type=float, default=10.0,
-                    help="seconds of the 64-viewer serving trace per mode (0 skips it)")
+    ap.add_argument("--serve", type=float, default=8.0,
+                    help="seconds of the 64-viewer serving trace per mode and load (0 skips it)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -352,17 +352,19 @@ def replay_alone(spec: ViewerSpec, pushed, pool: FramePool, device=None) -> Stre
 
 
 def serve_compare(n_viewers=64, duration_s=10.0, budget_gb=60.0, seed=0, frames_per_class=8,
-                  device=None, rate_hz=(72.0, 120.0), batch_launch=None, classes=CLASSES) -> dict:
+                  device=None, rate_hz=(72.0, 120.0), batch_launch=None, classes=CLASSES,
+                  n_streams=4, depth=2) -> dict:
     """Both modes on the same trace; returns their summaries."""
     dev = torch.device("cuda") if device is None else torch.device(device)
     specs = viewer_mix(n_viewers, duration_s, seed, rate_hz, classes)
     trace = arrivals(specs, seed)
     pool = FramePool(classes, frames_per_class, dev, seed)
     out = {"viewers": n_viewers, "duration_s": duration_s, "budget_gb": budget_gb,
-           "frames_offered": len(trace)}
+           "rate_hz": list(rate_hz), "frames_offered": len(trace),
+           "batched_streams": n_streams, "batched_depth": depth}
     for mode in ("batched", "plain"):
-        srv = Server(specs, pool, int(budget_gb * 1e9), mode=mode, device=dev,
-                     batch_launch=batch_launch)
+        srv = Server(specs, pool, int(budget_gb * 1e9), mode=mode, n_streams=n_streams, depth=depth,
+                     device=dev, batch_launch=batch_launch)
         out[mode] = srv.run(trace, duration_s).summary()
         srv.close()
         torch.cuda.synchronize(dev)
