@@ -490,7 +490,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="4k", choices=["4k", "4k_fp16", "hd", "hd_k8"])
+    ap.add_argument("--workload", default="4k", choices=["4k", "4k_fp16", "hd", "hd_k8", "tiny"])
     ap.add_argument("--distinct-frames", type=int, default=0,
                     help="frames resident in HBM (default: all of the workload's)")
     ap.add_argument("--pipe", type=int, default=1, help="1: pipelined kernel (default), 0: plain")
