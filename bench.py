@@ -35,17 +35,20 @@ METRIC = "4K reservoir update+resolve ms/frame, % HBM peak; served p99 latency v
 UNIT = "ms/frame"
 
 
-def algorithmic_bytes_per_px(K: int, fp16: bool) -> int:
+def algorithmic_bytes_per_px(K: int, fp16: bool, literal: bool = False) -> int:
     """Bytes every pixel-update moves: frame RGB in (12), resolved RGB out
     (12), W and P read and written (16), every slot's key, weight and colour
-    read (K * (8 + 3c))."""
+    read (K * (8 + 3c)). The literal n = 1 rule has no P and no key: 32 + 4 + 3c."""
     c = 2 if fp16 else 4
+    if literal:
+        return 32 + 4 + 3 * c
     return 40 + K * (8 + 3 * c)
 
 
-def replacement_bytes(fp16: bool) -> int:
-    """Bytes a replacement writes: key, sample index, weight and colour of the slot."""
-    return 12 + (6 if fp16 else 12)
+def replacement_bytes(fp16: bool, literal: bool = False) -> int:
+    """Bytes a replacement writes: key (not in the literal rule), sample index,
+    weight and colour of the slot."""
+    return (8 if literal else 12) + (6 if fp16 else 12)
 
 
 # ------------------------------------------------------------------ clocks
@@ -138,7 +141,7 @@ def oracle_ms_per_frame(spec, pixels: np.ndarray, frames: int, nthreads: int,
     import oracle
     st = oracle.OracleStream(spec.width, spec.height, spec.K, spec.r_f, seed=spec.seed,
                              stream_id=spec.stream_id, temporal_bias=spec.temporal_bias,
-                             pixels=pixels, nthreads=nthreads)
+                             pixels=pixels, nthreads=nthreads, rule=spec.update_rule)
     host = np.zeros((spec.height, spec.width, 3), np.float32)
     flat = host.reshape(-1, 3)
     pix_t = torch.as_tensor(pixels)
@@ -206,7 +209,7 @@ def run_reference(args, world, rank):
     import oracle
     st = oracle.OracleStream(spec.width, spec.height, spec.K, spec.r_f, seed=spec.seed,
                              stream_id=spec.stream_id, temporal_bias=spec.temporal_bias,
-                             pixels=pixels, nthreads=nthreads)
+                             pixels=pixels, nthreads=nthreads, rule=spec.update_rule)
     host = np.zeros((spec.height, spec.width, 3), np.float32)
     flat = host.reshape(-1, 3)
     pix_t = torch.as_tensor(pixels)
@@ -354,7 +357,7 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.Stream(device=dev)
     st = wrs.Stream(spec.width, spec.height, spec.K, spec.r_f, seed=seed, stream_id=spec.stream_id,
                     color_fp16=spec.color_fp16, temporal_bias=spec.temporal_bias, device=dev,
-                    stream=stream)
+                    stream=stream, update_rule=spec.update_rule)
     if args.block or args.px:
         st.set_launch(args.block, args.px)
     if args.pipe_px or args.pipe_stages or args.pipe_ctas or not args.pipe:
@@ -403,7 +406,8 @@ def run_ours(args, world, rank, local):
         d_out = torch.empty_like(out)
         st2 = wrs.Stream(spec.width, spec.height, spec.K, spec.r_f, seed=seed,
                          stream_id=spec.stream_id, color_fp16=spec.color_fp16,
-                         temporal_bias=spec.temporal_bias, device=dev, stream=stream)
+                         temporal_bias=spec.temporal_bias, device=dev, stream=stream,
+                         update_rule=spec.update_rule)
         torch.cuda.synchronize()
         for t in range(3):
             st2.push_frame_host(h_frames[t % pool], gaze[t % pool], h_out, d_in, d_out, stream=stream)
@@ -434,7 +438,9 @@ def run_ours(args, world, rank, local):
     torch.cuda.empty_cache()
 
     peaks = measured_peaks()
-    bpp = algorithmic_bytes_per_px(spec.K, spec.color_fp16) + rho * replacement_bytes(spec.color_fp16)
+    lit = spec.update_rule == 1
+    bpp = (algorithmic_bytes_per_px(spec.K, spec.color_fp16, lit)
+           + rho * replacement_bytes(spec.color_fp16, lit))
     achieved = bpp * hw / (kernel_avg * 1e-3) / 1e9
     kname = (f"{'pipe_kernel' if st_pipe[0] else 'push_kernel'}"
              f"<K={spec.K},{'fp16' if spec.color_fp16 else 'fp32'}>")
@@ -459,9 +465,9 @@ def run_ours(args, world, rank, local):
                      "traffic": recorded_traffic(kname, args.workload),
                      "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs, copy)",
                      "algorithmic_bytes_per_px": round(bpp, 2),
-                     "bytes_rule": f"{algorithmic_bytes_per_px(spec.K, spec.color_fp16)} B read/written by "
-                                   f"every pixel-update + replacement rate {rho:.4f} (counted on the device "
-                                   f"over the timed frames) x {replacement_bytes(spec.color_fp16)} B",
+                     "bytes_rule": f"{algorithmic_bytes_per_px(spec.K, spec.color_fp16, lit)} B read/written "
+                                   f"by every pixel-update + replacement rate {rho:.4f} (counted on the "
+                                   f"device over the timed frames) x {replacement_bytes(spec.color_fp16, lit)} B",
                      "kernel": kname},
         "replacement_rate": round(rho, 4),
         "pct_nominal_8tbs": round(100 * achieved / 8000.0, 2),
@@ -490,7 +496,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="4k", choices=["4k", "4k_fp16", "hd", "hd_k8", "tiny"])
+    ap.add_argument("--workload", default="4k",
+                    choices=["4k", "4k_fp16", "hd", "hd_k8", "tiny", "4k_k1", "4k_k1_literal"])
     ap.add_argument("--distinct-frames", type=int, default=0,
                     help="frames resident in HBM (default: all of the workload's)")
     ap.add_argument("--pipe", type=int, default=1, help="1: pipelined kernel (default), 0: plain")

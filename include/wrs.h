@@ -49,6 +49,8 @@ extern "C" {
 
 #define WRS_MAX_K 16
 #define WRS_MAX_BATCH 64  /* streams in one wrs_push_batch launch */
+#define WRS_RULE_KEYS 0
+#define WRS_RULE_LITERAL 1
 #define WRS_EMPTY_SLOT 0xFFFFFFFFu /* sample index of an unoccupied slot */
 
 typedef struct wrs_ctx wrs_ctx;
@@ -68,6 +70,10 @@ typedef struct {
                               accumulation stay FP32) */
   int32_t temporal_bias;   /* 1: apply Eq. (temporal-bias) before each combine (paper);
                               0: plain weighted sampling */
+  int32_t update_rule;     /* WRS_RULE_KEYS (0): exponential-key race over K slots;
+                              WRS_RULE_LITERAL (1): the paper's n = 1 update taken
+                              literally, Alg. 2 keeping R1 iff rand*(R1+R2) <= R1 after
+                              Eq. (temporal-bias); needs K == 1, uses no key or P plane */
 } wrs_config;
 
 /* Placement of the state planes inside the caller's state buffer. Every plane

@@ -48,7 +48,7 @@ def build(force: bool = False) -> str:
 class Config(C.Structure):
     _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("K", C.c_int32),
                 ("r_f", C.c_float), ("deg_per_px", C.c_float), ("seed", C.c_uint64),
-                ("stream_id", C.c_uint32), ("temporal_bias", C.c_int32)]
+                ("stream_id", C.c_uint32), ("temporal_bias", C.c_int32), ("rule", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -147,9 +147,13 @@ def uniforms(seed: int, stream_id: int, t: int, p0: int, n: int) -> np.ndarray:
     return u
 
 
-def make_config(width, height, K, r_f, deg_per_px=0.0, seed=0, stream_id=0, temporal_bias=True):
+RULE_KEYS, RULE_LITERAL = 0, 1
+
+
+def make_config(width, height, K, r_f, deg_per_px=0.0, seed=0, stream_id=0, temporal_bias=True,
+                rule=RULE_KEYS):
     return Config(int(width), int(height), int(K), float(r_f), float(deg_per_px), int(seed),
-                  int(stream_id), 1 if temporal_bias else 0)
+                  int(stream_id), 1 if temporal_bias else 0, int(rule))
 
 
 def weight_grid(cfg: Config, gx: float, gy: float) -> np.ndarray:
@@ -195,8 +199,9 @@ class OracleStream:
     """
 
     def __init__(self, width, height, K, r_f, deg_per_px=0.0, seed=0, stream_id=0,
-                 temporal_bias=True, pixels=None, nthreads=1):
-        self.cfg = make_config(width, height, K, r_f, deg_per_px, seed, stream_id, temporal_bias)
+                 temporal_bias=True, pixels=None, nthreads=1, rule=RULE_KEYS):
+        self.cfg = make_config(width, height, K, r_f, deg_per_px, seed, stream_id, temporal_bias,
+                               rule)
         self.K = int(K)
         self.pixels = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int64)
         n = width * height if self.pixels is None else len(self.pixels)

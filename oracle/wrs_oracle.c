@@ -263,6 +263,32 @@ void orc_pixel_step(int K, int bias, float w, float u, uint32_t t, const float r
   }
 }
 
+void orc_pixel_step_literal(int bias, float w, float u, uint32_t t, const float rgb_in[3],
+                            int flush, float* W, uint32_t* idx, float* wt, float* rgb) {
+  if (flush) {
+    *idx = ORC_EMPTY;
+    *wt = 0.0f;
+    rgb[0] = rgb[1] = rgb[2] = 0.0f;
+    *W = 0.0f;
+  }
+  /* Eq. (temporal-bias) on R1.wsum, the factor 1 - w/(W+w) evaluated as W/(W+w) */
+  if (bias && *W > 0.0f) {
+    float f = *W / (*W + w);
+    *W = *W * f;
+  }
+  /* Alg. 2 with R2 = the new sample alone: keep R1 iff rand * (R1 + R2) <= R1 */
+  float tot = *W + w;
+  if (!(u * tot <= *W)) {
+    *idx = t;
+    *wt = w;
+    rgb[0] = rgb_in[0];
+    rgb[1] = rgb_in[1];
+    rgb[2] = rgb_in[2];
+  }
+  /* R_out.wsum = R1.wsum + R2.wsum */
+  *W = tot;
+}
+
 void orc_resolve_pixel(int K, const uint32_t* idx, const float* wt, const float* rgb,
                        double out[3]) {
   /* out = sum_j wt_j c_j / sum_j wt_j over occupied slots. With K = 1 this is
@@ -318,8 +344,12 @@ static void push_range(orc_job* j) {
     float u = orc_uniform(c->seed, c->stream_id, j->t, p);
     const float* src = j->frame + (int64_t)y * j->pitch + 3 * (int64_t)x;
     int flush = j->fov_map ? (j->fov_map[p] == 0xFF) : 0;
-    orc_pixel_step(K, c->temporal_bias, w, u, j->t, src, flush, &j->W[i], &j->P[i],
-                   &j->key[i * K], &j->idx[i * K], &j->wt[i * K], &j->rgb[i * K * 3]);
+    if (c->rule == 1)
+      orc_pixel_step_literal(c->temporal_bias, w, u, j->t, src, flush, &j->W[i], &j->idx[i],
+                             &j->wt[i], &j->rgb[i * 3]);
+    else
+      orc_pixel_step(K, c->temporal_bias, w, u, j->t, src, flush, &j->W[i], &j->P[i],
+                     &j->key[i * K], &j->idx[i * K], &j->wt[i * K], &j->rgb[i * K * 3]);
   }
 }
 
@@ -352,6 +382,7 @@ int orc_push_frame(const orc_config* cfg, uint32_t t, const float* frame, int64_
                    const int64_t* pix, float* W, float* P, float* key, uint32_t* idx,
                    float* wt, float* rgb, int nthreads) {
   if (!cfg || !frame || cfg->width <= 0 || cfg->height <= 0 || cfg->K < 1 || cfg->K > 16 ||
+      (cfg->rule != 0 && cfg->rule != 1) || (cfg->rule == 1 && cfg->K != 1) ||
       pitch < 3 * (int64_t)cfg->width || !(cfg->r_f > 0.0f) || !isfinite(gx) || !isfinite(gy))
     return -1;
   int64_t hw = (int64_t)cfg->width * cfg->height;
@@ -424,16 +455,13 @@ void orc_run_streams(int K, int bias, int64_t n_trials, int n_items, const float
 
 void orc_chao_literal(int bias, int64_t n_trials, int n_items, const float* w,
                       const float* u, uint32_t* final_idx) {
+  const float zero[3] = {0.0f, 0.0f, 0.0f};
   for (int64_t i = 0; i < n_trials; ++i) {
-    uint32_t x = ORC_EMPTY; /* R1: sample */
-    float wsum = 0.0f;      /* R1.wsum */
-    for (int s = 0; s < n_items; ++s) {
-      float r2 = w[s];      /* R2 holds only the new candidate: R2.wsum = w_s */
-      if (bias && wsum > 0.0f) wsum = wsum * (1.0f - r2 / (wsum + r2)); /* Eq. (temporal-bias) */
-      float tot = wsum + r2;
-      if (!(u[i * n_items + s] * tot <= wsum)) x = (uint32_t)s; /* Alg. 2: R2 otherwise */
-      wsum = tot;
-    }
+    uint32_t x = ORC_EMPTY;
+    float W = 0.0f, wt = 0.0f, rgb[3];
+    for (int s = 0; s < n_items; ++s)
+      orc_pixel_step_literal(bias, w[s], u[i * n_items + s], (uint32_t)s, zero, 0, &W, &x, &wt,
+                             rgb);
     final_idx[i] = x;
   }
 }

@@ -30,6 +30,7 @@ typedef struct {
   uint64_t seed;           /* Philox key */
   uint32_t stream_id;      /* third Philox counter word */
   int32_t temporal_bias;   /* 1: apply Eq. (temporal-bias) before combining */
+  int32_t rule;            /* 0: key race over K slots; 1: literal Alg. 2 (K == 1) */
 } orc_config;
 
 /* FP32 exp for x in [-87, 0]: range reduction by ln 2 and a degree-7 Taylor
@@ -64,6 +65,14 @@ float orc_delta(const orc_config* cfg);
 void orc_pixel_step(int K, int bias, float w, float u, uint32_t t, const float rgb_in[3],
                     int flush, float* W, float* P, float* key, uint32_t* idx, float* wt,
                     float* rgb);
+/* The paper's n = 1 update taken literally: Eq. (temporal-bias) on R1.wsum,
+ * then Alg. 2 keeps R1 iff rand * (R1.wsum + R2.wsum) <= R1.wsum, else takes
+ * the new sample (R2 holds only it: R2.wsum = w). One slot, no key. Pinned:
+ * the selection law of Eq. (chao-selection-probability) with effective
+ * weights (statistics), and its distributional equality with the key race. */
+void orc_pixel_step_literal(int bias, float w, float u, uint32_t t, const float rgb_in[3],
+                            int flush, float* W, uint32_t* idx, float* wt, float* rgb);
+
 /* Weighted combination of the occupied slots, FP64. Pinned: K = 1 returns the
  * resident sample, equal colours return that colour, no slot returns 0. */
 void orc_resolve_pixel(int K, const uint32_t* idx, const float* wt, const float* rgb,

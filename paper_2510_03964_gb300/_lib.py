@@ -11,6 +11,7 @@ from . import build as _build
 WRS_OK, WRS_ERR_ARG, WRS_ERR_CUDA, WRS_ERR_BUDGET, WRS_ERR_TIMEOUT, WRS_ERR_STATE = range(6)
 WRS_MAX_K = 16
 WRS_MAX_BATCH = 64
+WRS_RULE_KEYS, WRS_RULE_LITERAL = 0, 1
 WRS_EMPTY_SLOT = 0xFFFFFFFF
 HEADER = os.path.join(_build.INCLUDE, "wrs.h")
 
@@ -18,7 +19,8 @@ HEADER = os.path.join(_build.INCLUDE, "wrs.h")
 class WrsConfig(C.Structure):
     _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("K", C.c_int32),
                 ("fovea_radius_px", C.c_float), ("deg_per_px", C.c_float), ("seed", C.c_uint64),
-                ("stream_id", C.c_uint32), ("color_fp16", C.c_int32), ("temporal_bias", C.c_int32)]
+                ("stream_id", C.c_uint32), ("color_fp16", C.c_int32), ("temporal_bias", C.c_int32),
+                ("update_rule", C.c_int32)]
 
 
 class WrsLayout(C.Structure):

@@ -108,15 +108,19 @@ __device__ __forceinline__ void issue_tile_copies(const StreamDev& s, const Fram
   const int64_t rem_plane = s.plane - p0, rem_px = s.hw - p0;
   const uint32_t n = static_cast<uint32_t>(rem_plane < T ? rem_plane : T);  // plane entries (x64)
   const uint32_t np = static_cast<uint32_t>(rem_px < T ? rem_px : T);       // pixels (x4)
+  // the literal rule (K = 1) reads no P and no key plane: copies 2 and 3 are skipped
+  const int skip = s.literal ? 2 : 0;
   const int ncopy = 3 + K + (resolve ? (cs == 2 ? 2 * K : K) : 0);
   if (lane == 0) {
     uint32_t bytes = 12u * np + 8u * n + 4u * K * n;
+    if (skip) bytes -= 4u * n + 4u * K * n;
     if (resolve) bytes += cs == 2 ? (4u * K * n + 8u * K * n) : 16u * K * n;
     mbar_arrive_expect_tx(bar, bytes + extra_tx);
   }
   __syncwarp();
   const int64_t pl = s.plane;
   for (int c = lane; c < ncopy; c += 32) {
+    if (skip && (c == 2 || c == 3)) continue;
     if (c == 0) {
       bulk_g2s(stage + L.frame, f.frame + 3 * p0, 12u * np, bar);
     } else if (c == 1) {
@@ -159,8 +163,9 @@ __device__ __forceinline__ void draw_tile_uniforms_warp(const StreamDev& s, cons
 }
 
 // Computes consumer thread `tid`'s PX pixels of a landed tile from shared
-// memory; returns how many of them replaced a slot.
-template <int KT, bool F16, int PX, int T>
+// memory; returns how many of them replaced a slot. LIT: the literal n = 1
+// rule (KT = 1).
+template <int KT, bool F16, int PX, int T, bool LIT = false>
 __device__ __forceinline__ int compute_tile(const StreamDev& s, const FrameDev& f,
                                             const StageLayout& L, const uint8_t* st,
                                             const float* u, int64_t p0, float d_f, int tid) {
@@ -177,8 +182,13 @@ __device__ __forceinline__ int compute_tile(const StreamDev& s, const FrameDev& 
   src.at = tl;
   src.frame = reinterpret_cast<const float*>(st + L.frame) + 3 * tl;
   src.u = u + tl;
-  if (f.fov != nullptr) return push_group<KT, F16, PX, true, true>(s, f, static_cast<int>(p), src, d_f);
-  return push_group<KT, F16, PX, true, false>(s, f, static_cast<int>(p), src, d_f);
+  if constexpr (LIT) {
+    if (f.fov != nullptr) return push_group_literal<F16, PX, true, true>(s, f, static_cast<int>(p), src, d_f);
+    return push_group_literal<F16, PX, true, false>(s, f, static_cast<int>(p), src, d_f);
+  } else {
+    if (f.fov != nullptr) return push_group<KT, F16, PX, true, true>(s, f, static_cast<int>(p), src, d_f);
+    return push_group<KT, F16, PX, true, false>(s, f, static_cast<int>(p), src, d_f);
+  }
 }
 
 // Adds a warp's counts to a running total: one atomic per warp.

@@ -34,7 +34,8 @@ struct BatchEntry {
   FrameDev f;
   uint32_t* status;
   int tile0;   // first global tile of this stream
-  int code;    // arithmetic variant: 0 K=4 f16, 1 K=8 f16, 2 K=4 f32, 3 K=8 f32, 4 any K f16, 5 any K f32
+  int code;    // arithmetic variant: 0 K=4 f16, 1 K=8 f16, 2 K=4 f32, 3 K=8 f32, 4 any K f16,
+               // 5 any K f32, 6 literal f16, 7 literal f32
 };
 
 struct BatchArgs {
@@ -58,7 +59,7 @@ __device__ __forceinline__ int entry_of(const BatchArgs& a, int g) {
 }
 
 __device__ __forceinline__ bool entry_f16(const BatchEntry& e) {
-  return e.code == 0 || e.code == 1 || e.code == 4;
+  return e.code == 0 || e.code == 1 || e.code == 4 || e.code == 6;
 }
 
 constexpr int kConsumerWarps = 8;
@@ -111,6 +112,8 @@ __global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
         case 2: rc = wrs::compute_tile<4, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 4, resolve), st, u, p0, d_f, tid); break;
         case 3: rc = wrs::compute_tile<8, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 4, resolve), st, u, p0, d_f, tid); break;
         case 4: rc = wrs::compute_tile<0, true, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 2, resolve), st, u, p0, d_f, tid); break;
+        case 6: rc = wrs::compute_tile<1, true, PX, T, true>(e.s, e.f, wrs::stage_layout(T, 1, 2, resolve), st, u, p0, d_f, tid); break;
+        case 7: rc = wrs::compute_tile<1, false, PX, T, true>(e.s, e.f, wrs::stage_layout(T, 1, 4, resolve), st, u, p0, d_f, tid); break;
         default: rc = wrs::compute_tile<0, false, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 4, resolve), st, u, p0, d_f, tid); break;
       }
       const unsigned c = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(rc));
@@ -219,6 +222,7 @@ extern "C" int wrs_batch_get_launch(const wrs_batch* b, int* px_per_thread, int*
 
 static int code_of(const wrs_config& c) {
   const bool f16 = c.color_fp16 != 0;
+  if (c.update_rule == WRS_RULE_LITERAL) return f16 ? 6 : 7;
   if (c.K == 4) return f16 ? 0 : 2;
   if (c.K == 8) return f16 ? 1 : 3;
   return f16 ? 4 : 5;

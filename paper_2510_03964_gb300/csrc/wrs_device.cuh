@@ -149,6 +149,7 @@ struct StreamDev {
   float delta;       // degrees per px
   uint32_t seed_lo, seed_hi, stream_id;
   int32_t bias;
+  int32_t literal;   // 1: the literal n = 1 rule (push_group_literal)
   unsigned long long* replacements;  // running count of slot replacements (stream header)
 };
 
@@ -597,6 +598,130 @@ __device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f,
 #pragma unroll
   for (int i = 0; i < PX; ++i) replaced += repl[i] ? 1 : 0;
   return replaced;
+}
+
+// The paper's n = 1 update taken literally (Sec. 4.2): Eq. (temporal-bias) on
+// W = R1.wsum, then Alg. 2 keeps R1 iff u * (W' + w) <= W', else takes the new
+// sample; W <- W' + w. One slot (K = 1), no key and no bias product: the P
+// and key planes are neither read nor written. Same frame, weight, uniform,
+// resolve and store code as the key race.
+template <bool F16, int PX, bool VEC, bool FOV>
+__device__ __forceinline__ int push_group_literal(const StreamDev& s, const FrameDev& f, int p0,
+                                                  const Src& src, float d_f) {
+  const int64_t pl = s.plane;
+  const int64_t ss = src.stride;
+  const int64_t sa = src.at;
+  bool valid[PX];
+  int xs[PX], ys[PX];
+  if constexpr (VEC) {
+    int y, x;
+    row_col(s, p0, y, x);
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+      valid[i] = true;
+      xs[i] = x + i;
+      ys[i] = y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+      const int p = p0 + i;
+      valid[i] = p < s.hw;
+      ys[i] = 0;
+      xs[i] = 0;
+      if (valid[i]) row_col(s, p, ys[i], xs[i]);
+    }
+  }
+  float rgb[PX][3];
+  if constexpr (VEC) {
+    load_rgb<PX>(src.frame, rgb);
+  } else {
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+      if (valid[i]) {
+        const float* fp = src.frame ? src.frame + 3 * i
+                                    : f.frame + static_cast<int64_t>(ys[i]) * f.pitch + 3 * xs[i];
+        rgb[i][0] = fp[0]; rgb[i][1] = fp[1]; rgb[i][2] = fp[2];
+      } else {
+        rgb[i][0] = rgb[i][1] = rgb[i][2] = 0.0f;
+      }
+    }
+  }
+  bool flush[PX];
+#pragma unroll
+  for (int i = 0; i < PX; ++i) flush[i] = FOV && valid[i] && f.fov[p0 + i] == 0xFFu;
+  static_assert(4 % PX == 0, "pixels per thread must divide 4");
+  float u[PX];
+  if (src.u != nullptr) {
+#pragma unroll
+    for (int i = 0; i < PX; ++i) u[i] = src.u[i];
+  } else {
+    const uint4 blk = philox4x32_10(
+        make_uint4(static_cast<uint32_t>(p0) >> 2, f.t, s.stream_id, 0u), s.seed_lo, s.seed_hi);
+#pragma unroll
+    for (int i = 0; i < PX; ++i) u[i] = unit_uniform(word(blk, (p0 + i) & 3));
+  }
+  float w[PX];
+#pragma unroll
+  for (int i = 0; i < PX; ++i) w[i] = valid[i] ? pixel_weight(s, d_f, xs[i], ys[i], f.gx, f.gy) : 1.0f;
+
+  float Wv[PX];
+  load_f<PX>(src.W + sa, Wv);
+  bool take[PX];
+#pragma unroll
+  for (int i = 0; i < PX; ++i) {
+    take[i] = false;
+    if (!valid[i]) continue;
+    if (flush[i]) Wv[i] = 0.0f;
+    if (s.bias && Wv[i] > 0.0f) Wv[i] = fmul(Wv[i], fdiv(Wv[i], fadd(Wv[i], w[i])));
+    const float tot = fadd(Wv[i], w[i]);
+    take[i] = !(fmul(u[i], tot) <= Wv[i]);  // Alg. 2: R1 kept on <=
+    Wv[i] = tot;
+  }
+
+  if (f.out != nullptr) {
+    float wv[PX], c0[PX], c1[PX], c2[PX];
+    load_slot<F16, PX>(src.wt, src.col, 1, 0, ss, sa, wv, c0, c1, c2);
+    float o[PX][3];
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+      float a = wv[i], r = c0[i], g = c1[i], b = c2[i];
+      if (take[i]) {
+        a = w[i];
+        r = stored_colour<F16>(rgb[i][0]);
+        g = stored_colour<F16>(rgb[i][1]);
+        b = stored_colour<F16>(rgb[i][2]);
+      }
+      const float num0 = __fmaf_rn(a, r, 0.0f), num1 = __fmaf_rn(a, g, 0.0f),
+                  num2 = __fmaf_rn(a, b, 0.0f);
+      const float den = fadd(0.0f, a);
+      const float inv = den > 0.0f ? __frcp_rn(den) : 0.0f;
+      o[i][0] = fmul(num0, inv);
+      o[i][1] = fmul(num1, inv);
+      o[i][2] = fmul(num2, inv);
+    }
+    if constexpr (VEC) {
+      store_rgb<PX>(f.out + (static_cast<int64_t>(ys[0]) * s.width + xs[0]) * 3, o);
+    } else {
+#pragma unroll
+      for (int i = 0; i < PX; ++i) {
+        if (!valid[i]) continue;
+        float* dst = f.out + static_cast<int64_t>(p0 + i) * 3;
+        dst[0] = o[i][0]; dst[1] = o[i][1]; dst[2] = o[i][2];
+      }
+    }
+  }
+  store_f<PX>(s.W + p0, Wv);
+  int taken = 0;
+#pragma unroll
+  for (int i = 0; i < PX; ++i) {
+    if (!valid[i] || !take[i]) continue;
+    const int64_t p = p0 + i;
+    s.idx[p] = f.t;
+    store_slot<F16>(s.wt, s.col, 1, 0, pl, p, w[i], rgb[i][0], rgb[i][1], rgb[i][2]);
+    taken += 1;
+  }
+  return taken;
 }
 
 // Standalone resolve of one group: the same accumulation as the fused resolve.

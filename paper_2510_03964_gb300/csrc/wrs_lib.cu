@@ -62,6 +62,10 @@ int wrs_check_config(const wrs_config* c) {
     return wrs_fail(WRS_ERR_ARG, "color_fp16 must be 0 or 1");
   if (c->temporal_bias != 0 && c->temporal_bias != 1)
     return wrs_fail(WRS_ERR_ARG, "temporal_bias must be 0 or 1");
+  if (c->update_rule != WRS_RULE_KEYS && c->update_rule != WRS_RULE_LITERAL)
+    return wrs_fail(WRS_ERR_ARG, "update_rule must be WRS_RULE_KEYS or WRS_RULE_LITERAL");
+  if (c->update_rule == WRS_RULE_LITERAL && c->K != 1)
+    return wrs_fail(WRS_ERR_ARG, "the literal update rule holds one sample: K must be 1");
   return WRS_OK;
 }
 
@@ -116,6 +120,7 @@ StreamDev wrs_stream_dev(const wrs_ctx* x) {
   s.seed_hi = static_cast<uint32_t>(x->cfg.seed >> 32);
   s.stream_id = x->cfg.stream_id;
   s.bias = x->cfg.temporal_bias;
+  s.literal = x->cfg.update_rule == WRS_RULE_LITERAL ? 1 : 0;
   s.replacements = reinterpret_cast<unsigned long long*>(x->state + x->lay.status_off + 8);
   return s;
 }
@@ -175,7 +180,7 @@ __global__ void zero_kernel(uint8_t* p, int64_t bytes) {
     reinterpret_cast<uint4*>(p)[i] = make_uint4(0, 0, 0, 0);
 }
 
-template <int KT, bool F16, int PX, bool VEC>
+template <int KT, bool F16, int PX, bool VEC, bool LIT>
 __global__ void __launch_bounds__(256, PX == 4 ? 2 : 3) push_kernel(const __grid_constant__ StreamDev s,
                                                       const __grid_constant__ FrameDev f) {
   __shared__ unsigned block_replaced;
@@ -187,10 +192,17 @@ __global__ void __launch_bounds__(256, PX == 4 ? 2 : 3) push_kernel(const __grid
   if (p0 < s.hw) {
     const float d_f = wrs::fovea_density(s);
     const wrs::Src src = wrs::global_src(s, f, static_cast<int>(p0), VEC);
-    if (f.fov != nullptr)
-      replaced = wrs::push_group<KT, F16, PX, VEC, true>(s, f, static_cast<int>(p0), src, d_f);
-    else
-      replaced = wrs::push_group<KT, F16, PX, VEC, false>(s, f, static_cast<int>(p0), src, d_f);
+    if constexpr (LIT) {
+      if (f.fov != nullptr)
+        replaced = wrs::push_group_literal<F16, PX, VEC, true>(s, f, static_cast<int>(p0), src, d_f);
+      else
+        replaced = wrs::push_group_literal<F16, PX, VEC, false>(s, f, static_cast<int>(p0), src, d_f);
+    } else {
+      if (f.fov != nullptr)
+        replaced = wrs::push_group<KT, F16, PX, VEC, true>(s, f, static_cast<int>(p0), src, d_f);
+      else
+        replaced = wrs::push_group<KT, F16, PX, VEC, false>(s, f, static_cast<int>(p0), src, d_f);
+    }
   }
   // one atomic per block for the stream's replacement count
   const unsigned c = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(replaced));
@@ -209,27 +221,28 @@ __global__ void __launch_bounds__(256, PX == 4 ? 2 : 3) resolve_kernel(const __g
   wrs::resolve_group<KT, F16, PX>(s, out, static_cast<int>(p0));
 }
 
-template <int KT, bool F16, int PX, bool VEC>
+template <int KT, bool F16, int PX, bool VEC, bool LIT = false>
 cudaError_t launch_push_t(const StreamDev& s, const FrameDev& f, int block, cudaStream_t st) {
   const int64_t groups = (static_cast<int64_t>(s.hw) + PX - 1) / PX;
   const int64_t grid = (groups + block - 1) / block;
-  push_kernel<KT, F16, PX, VEC><<<static_cast<unsigned>(grid), block, 0, st>>>(s, f);
+  push_kernel<KT, F16, PX, VEC, LIT><<<static_cast<unsigned>(grid), block, 0, st>>>(s, f);
   return cudaGetLastError();
 }
 
-template <int KT, bool F16>
+template <int KT, bool F16, bool LIT = false>
 cudaError_t launch_push_px(const StreamDev& s, const FrameDev& f, int block, int px,
                            cudaStream_t st) {
   switch (px) {
-    case 4: return launch_push_t<KT, F16, 4, true>(s, f, block, st);
-    case 2: return launch_push_t<KT, F16, 2, true>(s, f, block, st);
-    default: return launch_push_t<KT, F16, 1, false>(s, f, block, st);
+    case 4: return launch_push_t<KT, F16, 4, true, LIT>(s, f, block, st);
+    case 2: return launch_push_t<KT, F16, 2, true, LIT>(s, f, block, st);
+    default: return launch_push_t<KT, F16, 1, false, LIT>(s, f, block, st);
   }
 }
 
 template <bool F16>
 cudaError_t launch_push_k(const StreamDev& s, const FrameDev& f, int block, int px,
                           cudaStream_t st) {
+  if (s.literal) return launch_push_px<1, F16, true>(s, f, block, px, st);
   switch (s.K) {
     case 1: return launch_push_px<1, F16>(s, f, block, px, st);
     case 2: return launch_push_px<2, F16>(s, f, block, px, st);

@@ -44,7 +44,7 @@ constexpr int kPipeThreads = (kConsumerWarps + 1) * 32;
 // Warp-specialised: warps 0..7 compute (consumers, PX pixels per thread), warp 8
 // draws uniforms and issues copies (producer). Consumers and producer meet
 // only at the per-stage full/empty barriers, never at a block-wide barrier.
-template <int KT, bool F16, int PX>
+template <int KT, bool F16, int PX, bool LIT>
 __global__ void __launch_bounds__(kPipeThreads, PX == 1 ? 2 : 1)
     pipe_kernel(const __grid_constant__ StreamDev s, const __grid_constant__ FrameDev f,
                 const PipeArgs a) {
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kPipeThreads, PX == 1 ? 2 : 1)
     const float d_f = wrs::fovea_density(s);
     wrs::consume(r, my_tiles, a.timeout_ns, lane, [&](int it, const uint8_t* st, const float* u) {
       const int64_t p0 = static_cast<int64_t>(first + it * step) * T;
-      replaced += wrs::compute_tile<KT, F16, PX, T>(s, f, L, st, u, p0, d_f, tid);
+      replaced += wrs::compute_tile<KT, F16, PX, T, LIT>(s, f, L, st, u, p0, d_f, tid);
     });
   }
   __syncthreads();
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kPipeThreads, PX == 1 ? 2 : 1)
   }
 }
 
-template <int KT, bool F16, int PX>
+template <int KT, bool F16, int PX, bool LIT = false>
 cudaError_t launch_pipe_t(const StreamDev& s, const FrameDev& f, PipeArgs a, int sms,
                           int ctas_per_sm, cudaStream_t st) {
   constexpr int T = kConsumerWarps * 32 * PX;
@@ -103,13 +103,13 @@ cudaError_t launch_pipe_t(const StreamDev& s, const FrameDev& f, PipeArgs a, int
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (smem > configured[dev]) {
-    e = cudaFuncSetAttribute(pipe_kernel<KT, F16, PX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(pipe_kernel<KT, F16, PX, LIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     configured[dev] = smem;
   }
   int fit = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, pipe_kernel<KT, F16, PX>, kPipeThreads,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, pipe_kernel<KT, F16, PX, LIT>, kPipeThreads,
                                                     smem);
   if (e != cudaSuccess) return e;
   if (fit < 1) return cudaErrorInvalidConfiguration;
@@ -117,23 +117,24 @@ cudaError_t launch_pipe_t(const StreamDev& s, const FrameDev& f, PipeArgs a, int
   a.ntiles = static_cast<int>((static_cast<int64_t>(s.hw) + T - 1) / T);
   const int64_t want = static_cast<int64_t>(sms) * per_sm;
   const int grid = static_cast<int>(a.ntiles < want ? a.ntiles : want);
-  pipe_kernel<KT, F16, PX><<<grid, kPipeThreads, smem, st>>>(s, f, a);
+  pipe_kernel<KT, F16, PX, LIT><<<grid, kPipeThreads, smem, st>>>(s, f, a);
   return cudaGetLastError();
 }
 
-template <int KT, bool F16>
+template <int KT, bool F16, bool LIT = false>
 cudaError_t launch_pipe_px(const StreamDev& s, const FrameDev& f, const PipeArgs& a, int px,
                            int sms, int ctas, cudaStream_t st) {
   switch (px) {
-    case 4: return launch_pipe_t<KT, F16, 4>(s, f, a, sms, ctas, st);
-    case 2: return launch_pipe_t<KT, F16, 2>(s, f, a, sms, ctas, st);
-    default: return launch_pipe_t<KT, F16, 1>(s, f, a, sms, ctas, st);
+    case 4: return launch_pipe_t<KT, F16, 4, LIT>(s, f, a, sms, ctas, st);
+    case 2: return launch_pipe_t<KT, F16, 2, LIT>(s, f, a, sms, ctas, st);
+    default: return launch_pipe_t<KT, F16, 1, LIT>(s, f, a, sms, ctas, st);
   }
 }
 
 template <bool F16>
 cudaError_t launch_pipe_k(const StreamDev& s, const FrameDev& f, const PipeArgs& a, int px,
                           int sms, int ctas, cudaStream_t st) {
+  if (s.literal) return launch_pipe_px<1, F16, true>(s, f, a, px, sms, ctas, st);
   switch (s.K) {
     case 1: return launch_pipe_px<1, F16>(s, f, a, px, sms, ctas, st);
     case 2: return launch_pipe_px<2, F16>(s, f, a, px, sms, ctas, st);

@@ -30,10 +30,11 @@ def _dev_ptr(t: torch.Tensor | None, dtype, name: str):
 
 
 def make_config(width, height, K, fovea_radius_px, deg_per_px=0.0, seed=0, stream_id=0,
-                color_fp16=False, temporal_bias=True) -> WrsConfig:
+                color_fp16=False, temporal_bias=True, update_rule=0) -> WrsConfig:
+    """update_rule: 0 = exponential-key race over K slots, 1 = the literal n = 1 rule (K = 1)."""
     return WrsConfig(int(width), int(height), int(K), float(fovea_radius_px), float(deg_per_px),
                      int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream_id) & 0xFFFFFFFF,
-                     1 if color_fp16 else 0, 1 if temporal_bias else 0)
+                     1 if color_fp16 else 0, 1 if temporal_bias else 0, int(update_rule))
 
 
 def state_bytes(cfg: WrsConfig) -> int:
@@ -59,9 +60,9 @@ class Stream:
 
     def __init__(self, width, height, K, fovea_radius_px, deg_per_px=0.0, seed=0, stream_id=0,
                  color_fp16=False, temporal_bias=True, device=None, stream=None,
-                 state: torch.Tensor | None = None):
+                 state: torch.Tensor | None = None, update_rule: int = 0):
         self.cfg = make_config(width, height, K, fovea_radius_px, deg_per_px, seed, stream_id,
-                               color_fp16, temporal_bias)
+                               color_fp16, temporal_bias, update_rule)
         self.width, self.height, self.K = int(width), int(height), int(K)
         self.color_fp16 = bool(color_fp16)
         self.nbytes = state_bytes(self.cfg)

@@ -24,6 +24,7 @@ class StreamSpec:
     jitter_px: float = 6.0
     color_fp16: bool = False
     temporal_bias: bool = True
+    update_rule: int = 0   # 0: key race over K slots, 1: literal n = 1 rule (K = 1)
 
     @property
     def r_f(self) -> float:
@@ -81,6 +82,13 @@ WORKLOADS = {
         "hd_k8", "1920x1080 RGB FP32, 120 frames, K=8, fovea 120 px, rings as hd: the 4k slot "
         "layout at a quarter of the pixels (profiling case)",
         (StreamSpec(1920, 1080, 8, _RINGS_HD, seed=0, frames=120),)),
+    "4k_k1": Workload(
+        "4k_k1", "as 4k with one slot (n = 1, the paper's reservoir), exponential-key race",
+        (StreamSpec(3840, 2160, 1, _RINGS_4K, seed=0, frames=240),)),
+    "4k_k1_literal": Workload(
+        "4k_k1_literal", "as 4k_k1 with the literal n = 1 rule (rand * (R1 + R2) <= R1 keeps R1 "
+        "after the temporal bias; no keys, no bias product)",
+        (StreamSpec(3840, 2160, 1, _RINGS_4K, seed=0, frames=240, update_rule=1),)),
     "4k_fp16": Workload(
         "4k_fp16", "as 4k with FP16 colour planes (keys, weights and accumulation FP32)",
         (StreamSpec(3840, 2160, 8, _RINGS_4K, seed=0, frames=240, color_fp16=True),)),

@@ -79,7 +79,7 @@ class PairedRun:
     def __init__(self, width, height, K, r_f, radii=None, frames=8, seed=0, stream_id=0,
                  gaze_model="jitter", jitter_px=4.0, color_fp16=False, temporal_bias=True,
                  deg_per_px=0.0, pixels=None, launch=None, gaze=None, scene_seed=None,
-                 frame_device="cpu", pipeline=None):
+                 frame_device="cpu", pipeline=None, update_rule=0):
         self.width, self.height, self.K = width, height, K
         self.color_fp16 = color_fp16
         self.dev = torch.device("cuda")
@@ -92,14 +92,14 @@ class PairedRun:
         self.pixels = None if pixels is None else np.asarray(pixels, np.int64)
         self.gpu = wrs.Stream(width, height, K, r_f, deg_per_px=deg_per_px, seed=seed,
                               stream_id=stream_id, color_fp16=color_fp16,
-                              temporal_bias=temporal_bias, device=self.dev)
+                              temporal_bias=temporal_bias, device=self.dev, update_rule=update_rule)
         if launch:
             self.gpu.set_launch(*launch)
         if pipeline is not None:
             self.gpu.set_pipeline(*pipeline)
         self.orc = oracle.OracleStream(width, height, K, r_f, deg_per_px=deg_per_px, seed=seed,
                                        stream_id=stream_id, temporal_bias=temporal_bias,
-                                       pixels=self.pixels, nthreads=8)
+                                       pixels=self.pixels, nthreads=8, rule=update_rule)
         self.out = torch.empty((height, width, 3), dtype=torch.float32, device=self.dev)
         self._host_frame = None
 

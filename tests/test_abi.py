@@ -55,7 +55,8 @@ def test_state_bytes_and_layout(lib):
 
 @pytest.mark.parametrize("bad", [dict(width=0), dict(height=-1), dict(K=0), dict(K=17),
                                  dict(fovea_radius_px=0.0), dict(fovea_radius_px=float("inf")),
-                                 dict(deg_per_px=float("nan")), dict(width=1 << 16, height=1 << 15)])
+                                 dict(deg_per_px=float("nan")), dict(width=1 << 16, height=1 << 15),
+                                 dict(update_rule=2), dict(update_rule=1, K=2)])
 def test_invalid_configs_rejected(lib, bad):
     args = dict(width=64, height=64, K=4, fovea_radius_px=8.0)
     args.update(bad)

@@ -134,3 +134,28 @@ def test_mix16_workload_batch_equals_individual():
     for i in range(16):
         assert np.array_equal(mixed[i].export_raw(), solo[i].export_raw()), f"stream {i}"
     b.close()
+
+
+def test_batch_mixes_literal_and_key_streams():
+    dev = torch.device("cuda")
+    specs = [(96, 40, 1, False, 10.0), (64, 16, 4, True, 6.0), (128, 32, 1, True, 12.0)]
+    rules = [1, 0, 1]
+    frames = 6
+    data = _frames(specs, frames, seed0=40)
+    mk = lambda: [wrs.Stream(w, h, K, rf, seed=40 + i, stream_id=i, color_fp16=f16, device=dev,
+                             update_rule=rules[i]) for i, (w, h, K, f16, rf) in enumerate(specs)]
+    solo, mixed = mk(), mk()
+    b = wrs.Batch(4)
+    for t in range(frames):
+        for i, x in enumerate(solo):
+            x.push_frame(*data[i][t])
+        b.push(mixed, [d[t][0] for d in data], [d[t][1] for d in data])
+    torch.cuda.synchronize()
+    for i in range(len(specs)):
+        assert np.array_equal(mixed[i].export_raw(), solo[i].export_raw()), f"stream {i}"
+        assert mixed[i].replacements() == solo[i].replacements()
+    orc = oracle.OracleStream(96, 40, 1, 10.0, seed=40, stream_id=0, rule=1)
+    for t in range(frames):
+        orc.push_frame(data[0][t][0].cpu().numpy(), data[0][t][1])
+    compare_states(mixed[0].export_state(), orc.state(), None, False)
+    b.close()

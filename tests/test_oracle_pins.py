@@ -475,3 +475,42 @@ def test_push_frame_rejects_bad_arguments(orc):
         st.push_frame(np.zeros((4, 8, 3), np.float32), (float("nan"), 1.0))
     with pytest.raises(ValueError):
         st.push_frame(np.zeros((4, 8, 3), np.float32), (1.0, 1.0), pitch=10)
+
+
+def test_literal_rule_frame_path(orc):
+    """The literal n = 1 rule through the frame path: the first frame always
+    enters, W follows Eq. (temporal-bias) then Alg. 2's sum, a flush restarts
+    the pixel, and the key and P planes are never touched."""
+    st = _tiny_stream_rule(orc, rule=orc.RULE_LITERAL)
+    s = st.state()
+    assert np.all(s["idx"][:, 0] != orc.EMPTY) and np.all(s["idx"][:, 0] < 6)
+    assert np.all(np.isinf(s["key"])) and np.all(s["P"] == 1.0)
+    assert np.all((s["wt"][:, 0] > 0) & (s["wt"][:, 0] <= 1))
+    first = _tiny_stream_rule(orc, rule=orc.RULE_LITERAL, frames=1).state()
+    assert np.all(first["idx"][:, 0] == 0)
+    assert np.array_equal(first["W"], first["wt"][:, 0])
+    fl = _tiny_stream_rule(orc, rule=orc.RULE_LITERAL, flush_at=5).state()
+    flushed = (np.arange(37 * 23) % 37) < 18
+    assert np.all(fl["idx"][flushed, 0] == 5)
+    assert np.array_equal(fl["W"][flushed], fl["wt"][flushed, 0])
+
+
+def _tiny_stream_rule(orc, rule, frames=6, flush_at=None):
+    from synth import Foveator, gaze_path
+    w, h = 37, 23
+    fv = Foveator(w, h, (6.0, 12.0), seed=4)
+    gz = gaze_path(w, h, frames, seed=4, model="jitter", jitter_px=3.0)
+    st = orc.OracleStream(w, h, 1, r_f=6.0, seed=99, stream_id=2, rule=rule)
+    for t in range(frames):
+        fr, fm = fv.frame(*gz[t])
+        fm = fm.numpy().copy()
+        if flush_at is not None and t == flush_at:
+            fm[:, : w // 2] = 0xFF
+        st.push_frame(fr.numpy(), gz[t], fm)
+    return st
+
+
+def test_literal_rule_rejects_k_above_one(orc):
+    with pytest.raises(ValueError):
+        st = orc.OracleStream(8, 4, 2, r_f=2.0, rule=orc.RULE_LITERAL)
+        st.push_frame(np.zeros((4, 8, 3), np.float32), (1.0, 1.0))

@@ -236,3 +236,63 @@ def test_replacement_counter_matches_oracle(pipeline, fp16):
     torch.cuda.synchronize()
     run.compare()
     assert run.gpu.replacements() == expected
+
+
+@pytest.mark.parametrize("pipeline", [(True, 0, 0, 0), (True, 2, 2, 0), (False, 0, 0, 0)])
+@pytest.mark.parametrize("fp16", [False, True])
+def test_literal_rule_bit_exact(pipeline, fp16):
+    """The paper's n = 1 rule taken literally (rand * (R1 + R2) <= R1 keeps R1
+    after Eq. temporal-bias): planes bit-exact with the oracle, every frame."""
+    run = PairedRun(96, 40, 1, r_f=10.0, frames=10, seed=31, jitter_px=20, color_fp16=fp16,
+                    pipeline=pipeline, update_rule=1)
+    for t in range(10):
+        fm = None
+        if t == 6:
+            fm = np.zeros((40, 96), np.uint8)
+            fm[::3, ::5] = 0xFF
+        run.step(t, fov_map=fm)
+        torch.cuda.synchronize()
+        run.compare()
+
+
+@pytest.mark.parametrize("wh", [(37, 23), (1, 1), (5, 3)])
+def test_literal_rule_ragged(wh):
+    run = PairedRun(wh[0], wh[1], 1, r_f=3.0, frames=7, seed=32, jitter_px=5, update_rule=1)
+    run.run()
+    run.compare()
+
+
+def test_literal_rule_4k_sampled():
+    s = workload("4k").streams[0]
+    pix = _sample_pixels(s.width, s.height, 8192, 3)
+    run = PairedRun(s.width, s.height, 1, s.r_f, radii=s.radii, frames=60, seed=s.seed,
+                    gaze_model=s.gaze_model, jitter_px=s.jitter_px, pixels=pix, frame_device="cuda",
+                    update_rule=1)
+    run.run()
+    run.compare()
+
+
+def test_literal_rule_matches_key_race_in_distribution():
+    """With K = 1 the key race and the literal rule select with the same law:
+    whole image inside the fovea (w = 1), 24 frames, the final sample's frame
+    index over 12288 pixels (independent streams) is compared by a two-sample
+    chi-square at alpha = 1e-3."""
+    from scipy import stats
+    import paper_2510_03964_gb300 as wrs
+    w, h, frames = 128, 96, 24
+    dev = torch.device("cuda")
+    hist = []
+    for rule, seed in ((0, 101), (1, 202)):
+        st = wrs.Stream(w, h, 1, 1000.0, seed=seed, device=dev, update_rule=rule)
+        fr = torch.zeros((h, w, 3), device=dev)
+        for t in range(frames):
+            st.push_frame(fr, (w / 2, h / 2))
+        torch.cuda.synchronize()
+        idx = st.export_state()["idx"][0].astype(np.int64)
+        hist.append(np.bincount(idx, minlength=frames))
+    # the law itself: with equal weights under the bias, later frames are favoured
+    assert hist[0][-1] > hist[0][0] and hist[1][-1] > hist[1][0]
+    table = np.array(hist)
+    keep = table.sum(axis=0) >= 10
+    res = stats.chi2_contingency(table[:, keep])
+    assert res.pvalue > 1e-3
