@@ -69,6 +69,10 @@ typedef struct {
   int32_t color_fp16;      /* 0: FP32 slot colours; 1: FP16 slot colours (keys, weights and
                               accumulation stay FP32) */
   int32_t temporal_bias;   /* 1: apply Eq. (temporal-bias) before each combine (paper);
+                              2: Eq. (full-temporal-bias): also scale the history by
+                                 1 - |Delta L|, Delta L the CIELAB L* difference / 100
+                                 between the reservoir's resolved colour (linear sRGB, D65)
+                                 and the new sample; a factor of 0 acts as a flush;
                               0: plain weighted sampling */
   int32_t update_rule;     /* WRS_RULE_KEYS (0): exponential-key race over K slots;
                               WRS_RULE_LITERAL (1): the paper's n = 1 update taken

@@ -48,7 +48,8 @@ def build(force: bool = False) -> str:
 class Config(C.Structure):
     _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("K", C.c_int32),
                 ("r_f", C.c_float), ("deg_per_px", C.c_float), ("seed", C.c_uint64),
-                ("stream_id", C.c_uint32), ("temporal_bias", C.c_int32), ("rule", C.c_int32)]
+                ("stream_id", C.c_uint32), ("temporal_bias", C.c_int32), ("rule", C.c_int32),
+                ("color_fp16", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -83,6 +84,8 @@ def load():
                 "orc_density64_n": (None, [_P, _P, C.c_int64]),
                 "orc_uniform_n": (None, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, _P]),
                 "orc_weight32_grid": (None, [C.POINTER(Config), C.c_float, C.c_float, _P]),
+                "orc_lightness": (C.c_float, [C.c_float, C.c_float, C.c_float]),
+                "orc_lightness_n": (None, [_P, _P, C.c_int64]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -150,10 +153,21 @@ def uniforms(seed: int, stream_id: int, t: int, p0: int, n: int) -> np.ndarray:
 RULE_KEYS, RULE_LITERAL = 0, 1
 
 
+BIAS_NONE, BIAS_TEMPORAL, BIAS_FULL = 0, 1, 2
+
+
 def make_config(width, height, K, r_f, deg_per_px=0.0, seed=0, stream_id=0, temporal_bias=True,
-                rule=RULE_KEYS):
+                rule=RULE_KEYS, color_fp16=False):
+    """temporal_bias: False/True (Eq. temporal-bias) or BIAS_FULL (Eq. full-temporal-bias)."""
     return Config(int(width), int(height), int(K), float(r_f), float(deg_per_px), int(seed),
-                  int(stream_id), 1 if temporal_bias else 0, int(rule))
+                  int(stream_id), int(temporal_bias), int(rule), 1 if color_fp16 else 0)
+
+
+def lightness(rgb) -> np.ndarray:
+    rgb = np.ascontiguousarray(rgb, dtype=np.float32).reshape(-1, 3)
+    out = np.empty(len(rgb), np.float32)
+    load().orc_lightness_n(_ptr(rgb), _ptr(out), len(rgb))
+    return out
 
 
 def weight_grid(cfg: Config, gx: float, gy: float) -> np.ndarray:
@@ -199,9 +213,9 @@ class OracleStream:
     """
 
     def __init__(self, width, height, K, r_f, deg_per_px=0.0, seed=0, stream_id=0,
-                 temporal_bias=True, pixels=None, nthreads=1, rule=RULE_KEYS):
+                 temporal_bias=True, pixels=None, nthreads=1, rule=RULE_KEYS, color_fp16=False):
         self.cfg = make_config(width, height, K, r_f, deg_per_px, seed, stream_id, temporal_bias,
-                               rule)
+                               rule, color_fp16)
         self.K = int(K)
         self.pixels = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int64)
         n = width * height if self.pixels is None else len(self.pixels)

@@ -198,6 +198,51 @@ float orc_weight32(const orc_config* cfg, int32_t x, int32_t y, float gx, float 
   return w;
 }
 
+/* ---------------------------------------------------------------- lightness */
+
+/* CIE 1976 L*: 116 f(Y) - 16 with f(Y) = Y^(1/3) above (6/29)^3 and the
+ * linear segment (29/3)^3 Y below; Y from linear sRGB primaries (D65). */
+static const float LUMA_R = 0.2126f, LUMA_G = 0.7152f, LUMA_B = 0.0722f;
+static const float LAB_EPS = 216.0f / 24389.0f;   /* (6/29)^3 */
+static const float LAB_KAPPA = 24389.0f / 27.0f;  /* (29/3)^3 */
+static const float THIRD = 1.0f / 3.0f;
+
+float orc_lightness(float r, float g, float b) {
+  float Y = fmaf(LUMA_B, b, fmaf(LUMA_G, g, LUMA_R * r));
+  if (Y < 0.0f) Y = 0.0f;
+  if (Y > 1.0f) Y = 1.0f;
+  if (Y > LAB_EPS) {
+    float c = orc_exp(orc_log(Y) * THIRD);   /* Y^(1/3), Y in (eps, 1] */
+    return fmaf(116.0f, c, -16.0f);
+  }
+  return LAB_KAPPA * Y;
+}
+
+static float stored(float c, int fp16) { return fp16 ? (float)(_Float16)c : c; }
+
+float orc_lightness_factor(int K, const float* wt, const float* rgb, int fp16,
+                           const float rgb_in[3]) {
+  /* resolved colour of the slots before the push, in the GPU's FP32 order */
+  float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f, den = 0.0f;
+  for (int j = 0; j < K; ++j) {
+    n0 = fmaf(wt[j], stored(rgb[3 * j + 0], fp16), n0);
+    n1 = fmaf(wt[j], stored(rgb[3 * j + 1], fp16), n1);
+    n2 = fmaf(wt[j], stored(rgb[3 * j + 2], fp16), n2);
+    den = den + wt[j];
+  }
+  if (!(den > 0.0f)) return 1.0f;
+  float inv = 1.0f / den;
+  float L_old = orc_lightness(n0 * inv, n1 * inv, n2 * inv);
+  float L_new = orc_lightness(rgb_in[0], rgb_in[1], rgb_in[2]);
+  float dl = fabsf(L_old - L_new) * 0.01f;
+  if (dl > 1.0f) dl = 1.0f;
+  return 1.0f - dl;
+}
+
+void orc_lightness_n(const float* rgb, float* L, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) L[i] = orc_lightness(rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2]);
+}
+
 /* ---------------------------------------------------------------- reservoir */
 
 static const float P_FLOOR = 0x1p-64f;   /* renormalise the bias product below this */
@@ -206,6 +251,19 @@ static const float P_RESCALE = 0x1p64f;
 void orc_pixel_step(int K, int bias, float w, float u, uint32_t t, const float rgb_in[3],
                     int flush, float* W, float* P, float* key, uint32_t* idx, float* wt,
                     float* rgb) {
+  orc_pixel_step_full(K, bias, 0, w, u, t, rgb_in, flush, W, P, key, idx, wt, rgb);
+}
+
+void orc_pixel_step_full(int K, int bias, int fp16, float w, float u, uint32_t t,
+                         const float rgb_in[3], int flush, float* W, float* P, float* key,
+                         uint32_t* idx, float* wt, float* rgb) {
+  /* Eq. (full-temporal-bias): the history's weight also shrinks by 1 - |Delta L|;
+   * a factor of 0 leaves it no weight at all, which is a flush */
+  float g = 1.0f;
+  if (bias == 2 && !flush && *W > 0.0f) {
+    g = orc_lightness_factor(K, wt, rgb, fp16, rgb_in);
+    if (g <= 0.0f) flush = 1;
+  }
   if (flush) {
     /* occlusion / disocclusion: drop the history (Sec. 4.3, Sec. 6) */
     for (int j = 0; j < K; ++j) {
@@ -229,6 +287,7 @@ void orc_pixel_step(int K, int bias, float w, float u, uint32_t t, const float r
    * would be 0 * (1 - w/w)). */
   if (bias && *W > 0.0f) {
     float f = *W / (*W + w);
+    if (bias == 2) f = f * g;
     *W = *W * f;
     *P = *P * f;
     if (*P < P_FLOOR) {
@@ -265,6 +324,17 @@ void orc_pixel_step(int K, int bias, float w, float u, uint32_t t, const float r
 
 void orc_pixel_step_literal(int bias, float w, float u, uint32_t t, const float rgb_in[3],
                             int flush, float* W, uint32_t* idx, float* wt, float* rgb) {
+  orc_pixel_step_literal_full(bias, 0, w, u, t, rgb_in, flush, W, idx, wt, rgb);
+}
+
+void orc_pixel_step_literal_full(int bias, int fp16, float w, float u, uint32_t t,
+                                 const float rgb_in[3], int flush, float* W, uint32_t* idx,
+                                 float* wt, float* rgb) {
+  float g = 1.0f;
+  if (bias == 2 && !flush && *W > 0.0f) {
+    g = orc_lightness_factor(1, wt, rgb, fp16, rgb_in);
+    if (g <= 0.0f) flush = 1;
+  }
   if (flush) {
     *idx = ORC_EMPTY;
     *wt = 0.0f;
@@ -274,6 +344,7 @@ void orc_pixel_step_literal(int bias, float w, float u, uint32_t t, const float 
   /* Eq. (temporal-bias) on R1.wsum, the factor 1 - w/(W+w) evaluated as W/(W+w) */
   if (bias && *W > 0.0f) {
     float f = *W / (*W + w);
+    if (bias == 2) f = f * g;
     *W = *W * f;
   }
   /* Alg. 2 with R2 = the new sample alone: keep R1 iff rand * (R1 + R2) <= R1 */
@@ -345,11 +416,12 @@ static void push_range(orc_job* j) {
     const float* src = j->frame + (int64_t)y * j->pitch + 3 * (int64_t)x;
     int flush = j->fov_map ? (j->fov_map[p] == 0xFF) : 0;
     if (c->rule == 1)
-      orc_pixel_step_literal(c->temporal_bias, w, u, j->t, src, flush, &j->W[i], &j->idx[i],
-                             &j->wt[i], &j->rgb[i * 3]);
+      orc_pixel_step_literal_full(c->temporal_bias, c->color_fp16, w, u, j->t, src, flush,
+                                  &j->W[i], &j->idx[i], &j->wt[i], &j->rgb[i * 3]);
     else
-      orc_pixel_step(K, c->temporal_bias, w, u, j->t, src, flush, &j->W[i], &j->P[i],
-                     &j->key[i * K], &j->idx[i * K], &j->wt[i * K], &j->rgb[i * K * 3]);
+      orc_pixel_step_full(K, c->temporal_bias, c->color_fp16, w, u, j->t, src, flush, &j->W[i],
+                          &j->P[i], &j->key[i * K], &j->idx[i * K], &j->wt[i * K],
+                          &j->rgb[i * K * 3]);
   }
 }
 
@@ -383,6 +455,7 @@ int orc_push_frame(const orc_config* cfg, uint32_t t, const float* frame, int64_
                    float* wt, float* rgb, int nthreads) {
   if (!cfg || !frame || cfg->width <= 0 || cfg->height <= 0 || cfg->K < 1 || cfg->K > 16 ||
       (cfg->rule != 0 && cfg->rule != 1) || (cfg->rule == 1 && cfg->K != 1) ||
+      cfg->temporal_bias < 0 || cfg->temporal_bias > 2 ||
       pitch < 3 * (int64_t)cfg->width || !(cfg->r_f > 0.0f) || !isfinite(gx) || !isfinite(gy))
     return -1;
   int64_t hw = (int64_t)cfg->width * cfg->height;

@@ -29,8 +29,9 @@ typedef struct {
   float deg_per_px;        /* eccentricity per pixel in degrees; <= 0 selects 2.5 / r_f */
   uint64_t seed;           /* Philox key */
   uint32_t stream_id;      /* third Philox counter word */
-  int32_t temporal_bias;   /* 1: apply Eq. (temporal-bias) before combining */
+  int32_t temporal_bias;   /* 0: none; 1: Eq. (temporal-bias); 2: Eq. (full-temporal-bias) */
   int32_t rule;            /* 0: key race over K slots; 1: literal Alg. 2 (K == 1) */
+  int32_t color_fp16;      /* slot colours as the GPU stores them: 1 = rounded to IEEE half */
 } orc_config;
 
 /* FP32 exp for x in [-87, 0]: range reduction by ln 2 and a degree-7 Taylor
@@ -56,6 +57,18 @@ float orc_density32(float e);
 float orc_weight32(const orc_config* cfg, int32_t x, int32_t y, float gx, float gy);
 float orc_delta(const orc_config* cfg);
 
+/* CIELAB lightness L* of linear-light sRGB (D65) colour, fixed FP32 sequence:
+ * Y = 0.2126 r + 0.7152 g + 0.0722 b clamped to [0, 1]; L* = 116 Y^(1/3) - 16
+ * above (6/29)^3, else (29/3)^3 Y; the cube root as exp(ln(Y)/3) with orc_exp
+ * and orc_log. Pinned: L*(0) = 0, L*(1) = 100, 18% grey = 49.50, continuity at
+ * the junction. */
+float orc_lightness(float r, float g, float b);
+/* The factor 1 - |Delta L| of Eq. (full-temporal-bias), Delta L the L*
+ * difference / 100 between the reservoir's resolved colour before the push
+ * (FP32, slot order, as the GPU resolves) and the new sample. */
+float orc_lightness_factor(int K, const float* wt, const float* rgb, int fp16,
+                           const float rgb_in[3]);
+
 /* One candidate entering one pixel's reservoir: Eq. (temporal-bias) on the
  * history, then Alg. 2 in its exponential-key form (keep the K smallest keys
  * E/w scaled by the running bias product P). Pinned statistically:
@@ -65,6 +78,12 @@ float orc_delta(const orc_config* cfg);
 void orc_pixel_step(int K, int bias, float w, float u, uint32_t t, const float rgb_in[3],
                     int flush, float* W, float* P, float* key, uint32_t* idx, float* wt,
                     float* rgb);
+/* As orc_pixel_step; bias = 2 applies Eq. (full-temporal-bias): the history's
+ * weight is scaled by (1 - |Delta L|) as well (a factor of 0 drops the
+ * history, as a flush does). fp16: colours as stored in FP16 slots. */
+void orc_pixel_step_full(int K, int bias, int fp16, float w, float u, uint32_t t,
+                         const float rgb_in[3], int flush, float* W, float* P, float* key,
+                         uint32_t* idx, float* wt, float* rgb);
 /* The paper's n = 1 update taken literally: Eq. (temporal-bias) on R1.wsum,
  * then Alg. 2 keeps R1 iff rand * (R1.wsum + R2.wsum) <= R1.wsum, else takes
  * the new sample (R2 holds only it: R2.wsum = w). One slot, no key. Pinned:
@@ -72,6 +91,10 @@ void orc_pixel_step(int K, int bias, float w, float u, uint32_t t, const float r
  * weights (statistics), and its distributional equality with the key race. */
 void orc_pixel_step_literal(int bias, float w, float u, uint32_t t, const float rgb_in[3],
                             int flush, float* W, uint32_t* idx, float* wt, float* rgb);
+void orc_pixel_step_literal_full(int bias, int fp16, float w, float u, uint32_t t,
+                                 const float rgb_in[3], int flush, float* W, uint32_t* idx,
+                                 float* wt, float* rgb);
+void orc_lightness_n(const float* rgb, float* L, int64_t n);
 
 /* Weighted combination of the occupied slots, FP64. Pinned: K = 1 returns the
  * resident sample, equal colours return that colour, no slot returns 0. */

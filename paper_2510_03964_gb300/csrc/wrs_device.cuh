@@ -178,6 +178,34 @@ __device__ __forceinline__ void row_col(const StreamDev& s, int p, int& y, int& 
   x = r;
 }
 
+// CIE 1976 lightness L* of linear-light sRGB (D65): Y = 0.2126 r + 0.7152 g +
+// 0.0722 b clamped to [0, 1]; 116 Y^(1/3) - 16 above (6/29)^3 (cube root as
+// exp(ln Y / 3) with the routines above), (29/3)^3 Y below.
+constexpr float kLumaR = 0.2126f, kLumaG = 0.7152f, kLumaB = 0.0722f;
+constexpr float kLabEps = 0x1.22354ep-7f;     // float nearest (6/29)^3 = 216/24389
+constexpr float kLabKappa = 0x1.c3a5eep+9f;   // float nearest (29/3)^3 = 24389/27
+constexpr float kThird = 0x1.555556p-2f;      // float nearest 1/3
+
+__device__ __forceinline__ float lightness(float r, float g, float b) {
+  float Y = ffma(kLumaB, b, ffma(kLumaG, g, fmul(kLumaR, r)));
+  Y = fminf(fmaxf(Y, 0.0f), 1.0f);
+  if (Y > kLabEps) return ffma(116.0f, exp_nonpos(fmul(log_pos(Y), kThird)), -16.0f);
+  return fmul(kLabKappa, Y);
+}
+
+// The factor 1 - |Delta L| of Eq. (full-temporal-bias): Delta L is the L*
+// difference / 100 (clamped to 1) between the resolved colour of the slots
+// before the push and the new sample.
+__device__ __forceinline__ float lightness_factor(float n0, float n1, float n2, float den,
+                                                  const float (&rgb)[3]) {
+  if (!(den > 0.0f)) return 1.0f;
+  const float inv = __frcp_rn(den);
+  const float l_old = lightness(fmul(n0, inv), fmul(n1, inv), fmul(n2, inv));
+  const float l_new = lightness(rgb[0], rgb[1], rgb[2]);
+  const float dl = fminf(fmul(fabsf(fsub(l_old, l_new)), 0.01f), 1.0f);
+  return fsub(1.0f, dl);
+}
+
 // density at the fovea edge, the normaliser of Eq. (phat)
 __device__ __forceinline__ float fovea_density(const StreamDev& s) {
   return density(fminf(fmul(s.r_f, s.delta), kEccMax));
@@ -304,10 +332,11 @@ __device__ __forceinline__ float stored_colour(float c) {
 // k * P of the new candidate; `rescale` reports a 2^64 rescale of P (the
 // stored keys must then be rescaled by the same factor).
 __device__ __forceinline__ float bias_and_sum(int bias, float w, float k, float& W, float& P,
-                                              bool& rescale) {
+                                              bool& rescale, float g = 1.0f) {
   rescale = false;
   if (bias && W > 0.0f) {
-    const float fb = fdiv(W, fadd(W, w));  // 1 - w / (W + w)
+    float fb = fdiv(W, fadd(W, w));  // 1 - w / (W + w)
+    if (bias == 2) fb = fmul(fb, g);  // Eq. (full-temporal-bias): times 1 - |Delta L|
     W = fmul(W, fb);
     P = fmul(P, fb);
     if (P < kPFloor) {
@@ -490,6 +519,32 @@ __device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f,
   float Wv[PX], Pv[PX];
   load_f<PX>(src.W + sa, Wv);
   load_f<PX>(src.P + sa, Pv);
+  float gl[PX];
+#pragma unroll
+  for (int i = 0; i < PX; ++i) gl[i] = 1.0f;
+  if (s.bias == 2) {
+    // Eq. (full-temporal-bias): resolved colour of the slots before the push
+    float n0[PX], n1[PX], n2[PX], dn[PX];
+#pragma unroll
+    for (int i = 0; i < PX; ++i) { n0[i] = n1[i] = n2[i] = dn[i] = 0.0f; }
+    for (int j = 0; j < K; ++j) {
+      float a[PX], r[PX], g[PX], b[PX];
+      load_slot<F16, PX>(src.wt, src.col, K, j, ss, sa, a, r, g, b);
+#pragma unroll
+      for (int i = 0; i < PX; ++i) {
+        n0[i] = __fmaf_rn(a[i], r[i], n0[i]);
+        n1[i] = __fmaf_rn(a[i], g[i], n1[i]);
+        n2[i] = __fmaf_rn(a[i], b[i], n2[i]);
+        dn[i] = fadd(dn[i], a[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+      if (!valid[i] || flush[i] || !(Wv[i] > 0.0f)) continue;
+      gl[i] = lightness_factor(n0[i], n1[i], n2[i], dn[i], rgb[i]);
+      if (gl[i] <= 0.0f) flush[i] = true;  // no weight left in the history
+    }
+  }
   bool rescale[PX];
   float ks[PX];
 #pragma unroll
@@ -497,7 +552,7 @@ __device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f,
     rescale[i] = false;
     if (!valid[i]) { ks[i] = kInf; continue; }
     if (flush[i]) { Wv[i] = 0.0f; Pv[i] = 1.0f; }
-    ks[i] = bias_and_sum(s.bias, w[i], k[i], Wv[i], Pv[i], rescale[i]);
+    ks[i] = bias_and_sum(s.bias, w[i], k[i], Wv[i], Pv[i], rescale[i], gl[i]);
   }
 
   // key race: the slot holding the largest key (lowest index on ties; an empty
@@ -667,13 +722,32 @@ __device__ __forceinline__ int push_group_literal(const StreamDev& s, const Fram
 
   float Wv[PX];
   load_f<PX>(src.W + sa, Wv);
+  float gl[PX];
+#pragma unroll
+  for (int i = 0; i < PX; ++i) gl[i] = 1.0f;
+  if (s.bias == 2) {
+    // Eq. (full-temporal-bias): Delta L against the resident sample
+    float a[PX], r[PX], g[PX], b[PX];
+    load_slot<F16, PX>(src.wt, src.col, 1, 0, ss, sa, a, r, g, b);
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+      if (!valid[i] || flush[i] || !(Wv[i] > 0.0f)) continue;
+      gl[i] = lightness_factor(__fmaf_rn(a[i], r[i], 0.0f), __fmaf_rn(a[i], g[i], 0.0f),
+                               __fmaf_rn(a[i], b[i], 0.0f), fadd(0.0f, a[i]), rgb[i]);
+      if (gl[i] <= 0.0f) flush[i] = true;
+    }
+  }
   bool take[PX];
 #pragma unroll
   for (int i = 0; i < PX; ++i) {
     take[i] = false;
     if (!valid[i]) continue;
     if (flush[i]) Wv[i] = 0.0f;
-    if (s.bias && Wv[i] > 0.0f) Wv[i] = fmul(Wv[i], fdiv(Wv[i], fadd(Wv[i], w[i])));
+    if (s.bias && Wv[i] > 0.0f) {
+      float fb = fdiv(Wv[i], fadd(Wv[i], w[i]));
+      if (s.bias == 2) fb = fmul(fb, gl[i]);
+      Wv[i] = fmul(Wv[i], fb);
+    }
     const float tot = fadd(Wv[i], w[i]);
     take[i] = !(fmul(u[i], tot) <= Wv[i]);  // Alg. 2: R1 kept on <=
     Wv[i] = tot;

@@ -60,8 +60,8 @@ int wrs_check_config(const wrs_config* c) {
     return wrs_fail(WRS_ERR_ARG, "deg_per_px must be finite");
   if (c->color_fp16 != 0 && c->color_fp16 != 1)
     return wrs_fail(WRS_ERR_ARG, "color_fp16 must be 0 or 1");
-  if (c->temporal_bias != 0 && c->temporal_bias != 1)
-    return wrs_fail(WRS_ERR_ARG, "temporal_bias must be 0 or 1");
+  if (c->temporal_bias < 0 || c->temporal_bias > 2)
+    return wrs_fail(WRS_ERR_ARG, "temporal_bias must be 0, 1 or 2");
   if (c->update_rule != WRS_RULE_KEYS && c->update_rule != WRS_RULE_LITERAL)
     return wrs_fail(WRS_ERR_ARG, "update_rule must be WRS_RULE_KEYS or WRS_RULE_LITERAL");
   if (c->update_rule == WRS_RULE_LITERAL && c->K != 1)

@@ -31,10 +31,11 @@ def _dev_ptr(t: torch.Tensor | None, dtype, name: str):
 
 def make_config(width, height, K, fovea_radius_px, deg_per_px=0.0, seed=0, stream_id=0,
                 color_fp16=False, temporal_bias=True, update_rule=0) -> WrsConfig:
-    """update_rule: 0 = exponential-key race over K slots, 1 = the literal n = 1 rule (K = 1)."""
+    """update_rule: 0 = exponential-key race over K slots, 1 = the literal n = 1 rule (K = 1).
+    temporal_bias: False/True (Eq. temporal-bias) or 2 (Eq. full-temporal-bias)."""
     return WrsConfig(int(width), int(height), int(K), float(fovea_radius_px), float(deg_per_px),
                      int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream_id) & 0xFFFFFFFF,
-                     1 if color_fp16 else 0, 1 if temporal_bias else 0, int(update_rule))
+                     1 if color_fp16 else 0, int(temporal_bias), int(update_rule))
 
 
 def state_bytes(cfg: WrsConfig) -> int:

@@ -79,13 +79,17 @@ class PairedRun:
     def __init__(self, width, height, K, r_f, radii=None, frames=8, seed=0, stream_id=0,
                  gaze_model="jitter", jitter_px=4.0, color_fp16=False, temporal_bias=True,
                  deg_per_px=0.0, pixels=None, launch=None, gaze=None, scene_seed=None,
-                 frame_device="cpu", pipeline=None, update_rule=0):
+                 frame_device="cpu", pipeline=None, update_rule=0, switch_scene_at=None):
         self.width, self.height, self.K = width, height, K
         self.color_fp16 = color_fp16
         self.dev = torch.device("cuda")
         radii = radii or (r_f, 2.5 * r_f)
         self.fv = Foveator(width, height, radii, seed=seed if scene_seed is None else scene_seed,
                            device=frame_device)
+        # a scene cut: from frame switch_scene_at on, frames come from another scene
+        self.switch_at = switch_scene_at
+        self.fv2 = None if switch_scene_at is None else Foveator(width, height, radii, seed=seed + 1000,
+                                                                  device=frame_device)
         if gaze is None:
             gaze = gaze_path(width, height, frames, seed=seed, model=gaze_model, jitter_px=jitter_px)
         self.gaze = np.asarray(gaze, np.float32)
@@ -99,13 +103,15 @@ class PairedRun:
             self.gpu.set_pipeline(*pipeline)
         self.orc = oracle.OracleStream(width, height, K, r_f, deg_per_px=deg_per_px, seed=seed,
                                        stream_id=stream_id, temporal_bias=temporal_bias,
-                                       pixels=self.pixels, nthreads=8, rule=update_rule)
+                                       pixels=self.pixels, nthreads=8, rule=update_rule,
+                                       color_fp16=color_fp16)
         self.out = torch.empty((height, width, 3), dtype=torch.float32, device=self.dev)
         self._host_frame = None
 
     def step(self, t, fov_map=None, fused=True, pitch_pad=0):
         gx, gy = self.gaze[t]
-        fr, _ = self.fv.frame(float(gx), float(gy))
+        fv = self.fv2 if (self.switch_at is not None and t >= self.switch_at) else self.fv
+        fr, _ = fv.frame(float(gx), float(gy))
         fm_d = None if fov_map is None else torch.as_tensor(fov_map).to(self.dev)
         if pitch_pad:
             padded = torch.zeros((self.height, 3 * self.width + pitch_pad), dtype=torch.float32)

@@ -514,3 +514,59 @@ def test_literal_rule_rejects_k_above_one(orc):
     with pytest.raises(ValueError):
         st = orc.OracleStream(8, 4, 2, r_f=2.0, rule=orc.RULE_LITERAL)
         st.push_frame(np.zeros((4, 8, 3), np.float32), (1.0, 1.0))
+
+
+# ------------------------------------------------------------------ full temporal bias
+
+def test_lightness_special_values(orc):
+    """CIE 1976 L*: 0 for black, 100 for white, 49.50 for 18% grey, continuous
+    at the (6/29)^3 junction (both branches give 8), increasing in Y."""
+    L = orc.lightness([[0, 0, 0], [1, 1, 1], [0.18, 0.18, 0.18]])
+    assert L[0] == 0.0 and L[1] == pytest.approx(100.0, abs=1e-4)
+    assert L[2] == pytest.approx(49.496, abs=2e-3)
+    e = (6.0 / 29.0) ** 3
+    lo, hi = orc.lightness([[e * 0.99999] * 3, [e * 1.00001] * 3])
+    assert lo == pytest.approx(8.0, abs=1e-3) and hi == pytest.approx(8.0, abs=1e-3)
+    y = np.linspace(0, 1, 2001)
+    Ly = orc.lightness(np.repeat(y[:, None], 3, axis=1))
+    assert np.all(np.diff(Ly) >= -1e-4)
+    # luminance weights of sRGB primaries: pure green is lighter than pure red and blue
+    r, g, b = orc.lightness(np.eye(3))
+    assert g > r > b > 0
+
+
+def _full_bias_pair(orc, colours, weights_inside=True, K=1, rule=0):
+    """Two streams over the same 4x1 frames of uniform colour: Eq. (temporal-bias)
+    and Eq. (full-temporal-bias)."""
+    out = []
+    for bias in (1, 2):
+        st = orc.OracleStream(4, 1, K, r_f=100.0, seed=5, temporal_bias=bias, rule=rule)
+        for c in colours:
+            st.push_frame(np.tile(np.float32(c), (1, 4, 1)), (2.0, 0.5))
+        out.append(st.state())
+    return out
+
+
+def test_full_bias_without_colour_change_is_temporal_bias(orc):
+    for K, rule in ((1, 0), (4, 0), (1, 1)):
+        a, b = _full_bias_pair(orc, [[0.3, 0.5, 0.2]] * 9, K=K, rule=rule)
+        for k in a:
+            assert np.array_equal(a[k], b[k]), (K, rule, k)
+
+
+def test_full_bias_weight_recursion(orc):
+    """Frame 0 black, frame 1 18% grey, w = 1 for both (inside the fovea):
+    W1 = W0 (W0 / (W0 + w)) (1 - |Delta L|) + w with Delta L = (49.496 - 0)/100."""
+    a, b = _full_bias_pair(orc, [[0, 0, 0], [0.18, 0.18, 0.18]])
+    dl = 0.49496
+    assert a["W"][0] == pytest.approx(1.0 * 0.5 + 1.0, rel=1e-6)
+    assert b["W"][0] == pytest.approx(1.0 * 0.5 * (1 - dl) + 1.0, rel=1e-4)
+
+
+def test_full_bias_total_change_flushes(orc):
+    """Black to white is |Delta L| = 1: the history keeps no weight, as after a flush."""
+    for K, rule in ((1, 0), (4, 0), (1, 1)):
+        _, b = _full_bias_pair(orc, [[0, 0, 0]] * 5 + [[1, 1, 1]], K=K, rule=rule)
+        assert np.all(b["idx"][:, 0] == 5)
+        assert np.all(b["idx"][:, 1:] == orc.EMPTY)
+        assert np.array_equal(b["W"], b["wt"][:, 0])

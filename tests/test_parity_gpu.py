@@ -296,3 +296,29 @@ def test_literal_rule_matches_key_race_in_distribution():
     keep = table.sum(axis=0) >= 10
     res = stats.chi2_contingency(table[:, keep])
     assert res.pvalue > 1e-3
+
+
+@pytest.mark.parametrize("K,rule,fp16,pipeline", [
+    (1, 0, False, (True, 0, 0, 0)), (4, 0, False, (True, 0, 0, 0)), (8, 0, True, (True, 0, 0, 0)),
+    (4, 0, False, (False, 0, 0, 0)), (1, 1, False, (True, 0, 0, 0)), (1, 1, True, (False, 0, 0, 0)),
+    (3, 0, True, (True, 2, 2, 0))])
+def test_full_temporal_bias_bit_exact(K, rule, fp16, pipeline):
+    """Eq. (full-temporal-bias) across a scene cut at frame 6 (large Delta L):
+    planes bit-exact with the oracle before, at and after the cut."""
+    run = PairedRun(96, 40, K, r_f=10.0, frames=12, seed=41, jitter_px=20, color_fp16=fp16,
+                    pipeline=pipeline, update_rule=rule, temporal_bias=2, switch_scene_at=6)
+    for t in range(12):
+        run.step(t)
+        if t in (5, 6, 7, 11):
+            torch.cuda.synchronize()
+            run.compare()
+
+
+def test_full_temporal_bias_4k_sampled():
+    s = workload("4k").streams[0]
+    pix = _sample_pixels(s.width, s.height, 8192, 4)
+    run = PairedRun(s.width, s.height, s.K, s.r_f, radii=s.radii, frames=40, seed=s.seed,
+                    gaze_model=s.gaze_model, jitter_px=s.jitter_px, pixels=pix, frame_device="cuda",
+                    temporal_bias=2, switch_scene_at=20)
+    run.run()
+    run.compare()
