@@ -86,6 +86,9 @@ def load():
                 "orc_weight32_grid": (None, [C.POINTER(Config), C.c_float, C.c_float, _P]),
                 "orc_lightness": (C.c_float, [C.c_float, C.c_float, C.c_float]),
                 "orc_lightness_n": (None, [_P, _P, C.c_int64]),
+                "orc_mip_means": (None, [_P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, _P]),
+                "orc_foveate": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, _P,
+                                          C.c_float, C.c_float, C.c_int32, _P, _P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -200,6 +203,38 @@ def chao_literal(bias: bool, w, u) -> np.ndarray:
     idx = np.empty(n_trials, dtype=np.uint32)
     load().orc_chao_literal(1 if bias else 0, n_trials, n_items, _ptr(w), _ptr(u), _ptr(idx))
     return idx
+
+
+# ------------------------------------------------------------ foveation
+
+FILTER_BOX, FILTER_BILINEAR = 0, 1
+
+
+def mip_means(img: np.ndarray, level: int) -> np.ndarray:
+    """Level-`level` block means of an RGB float32 image [h][w][3] (or [h][pitch])."""
+    img = _f32(img)
+    h = img.shape[0]
+    w = img.shape[1] if img.ndim == 3 else None
+    if w is None:
+        raise ValueError("pass the image as [h][w][3]")
+    hb, wb = -(-h // (1 << level)), -(-w // (1 << level))
+    out = np.empty((hb, wb, 3), np.float32)
+    load().orc_mip_means(_ptr(img), 3 * w, w, h, level, _ptr(out))
+    return out
+
+
+def foveate(img: np.ndarray, radii, gx: float, gy: float, filter: int = FILTER_BOX):
+    """(frame float32 [h][w][3], ring map uint8 [h][w]) of the foveation post-process."""
+    img = _f32(img)
+    h, w = img.shape[:2]
+    r = _f32(list(radii))
+    frame = np.empty((h, w, 3), np.float32)
+    ring = np.empty((h, w), np.uint8)
+    rc = load().orc_foveate(_ptr(img), 3 * w, w, h, len(r), _ptr(r), float(gx), float(gy),
+                            int(filter), _ptr(frame), _ptr(ring))
+    if rc != 0:
+        raise ValueError("oracle rejected the foveation arguments")
+    return frame, ring
 
 
 # ------------------------------------------------------------ streams

@@ -539,6 +539,103 @@ void orc_chao_literal(int bias, int64_t n_trials, int n_items, const float* w,
   }
 }
 
+/* ---------------------------------------------------------------- foveation */
+
+/* Sum of channel c over the aligned 2^L block (by, bx): the quad tree of its
+ * four quadrants, top pair then bottom pair, each pair left then right. */
+static float block_sum(const float* img, int64_t pitch, int32_t w, int32_t h, int32_t L,
+                       int64_t by, int64_t bx, int c) {
+  if (L == 0) return (by < h && bx < w) ? img[by * pitch + 3 * bx + c] : 0.0f;
+  float s00 = block_sum(img, pitch, w, h, L - 1, 2 * by, 2 * bx, c);
+  float s01 = block_sum(img, pitch, w, h, L - 1, 2 * by, 2 * bx + 1, c);
+  float s10 = block_sum(img, pitch, w, h, L - 1, 2 * by + 1, 2 * bx, c);
+  float s11 = block_sum(img, pitch, w, h, L - 1, 2 * by + 1, 2 * bx + 1, c);
+  float top = s00 + s01;
+  float bot = s10 + s11;
+  return top + bot;
+}
+
+static int64_t ceil_shift(int64_t n, int L) { return (n + ((int64_t)1 << L) - 1) >> L; }
+
+void orc_mip_means(const float* img, int64_t pitch, int32_t w, int32_t h, int32_t L, float* out) {
+  const int64_t b = (int64_t)1 << L;
+  const int64_t hb = ceil_shift(h, L), wb = ceil_shift(w, L);
+  for (int64_t by = 0; by < hb; ++by)
+    for (int64_t bx = 0; bx < wb; ++bx) {
+      int64_t rows = (by * b + b < h ? by * b + b : h) - by * b;
+      int64_t cols = (bx * b + b < w ? bx * b + b : w) - bx * b;
+      float n = (float)(rows * cols);
+      for (int c = 0; c < 3; ++c)
+        out[(by * wb + bx) * 3 + c] = block_sum(img, pitch, w, h, L, by, bx, c) / n;
+    }
+}
+
+/* Level coordinate of pixel index i at level L, clamped to [0, nb - 1]:
+ * integer part i0, neighbour i1 and fraction f. */
+static void texel_coord(int32_t i, int32_t L, int64_t nb, int64_t* i0, int64_t* i1, float* f) {
+  float inv_b = 1.0f / (float)(1 << L);
+  float u = ((float)i + 0.5f) * inv_b - 0.5f;
+  if (u < 0.0f) u = 0.0f;
+  if (u > (float)(nb - 1)) u = (float)(nb - 1);
+  float fl = floorf(u);
+  *i0 = (int64_t)fl;
+  *i1 = *i0 + 1 < nb ? *i0 + 1 : nb - 1;
+  *f = u - fl;
+}
+
+int orc_foveate(const float* img, int64_t pitch, int32_t w, int32_t h, int32_t nradii,
+                const float* radii, float gx, float gy, int32_t filter, float* frame,
+                uint8_t* ring_map) {
+  if (!img || !frame || w < 1 || h < 1 || pitch < 3 * (int64_t)w) return -1;
+  if (nradii < 1 || nradii > ORC_MAX_MIP_LEVELS - 1 || !radii) return -1;
+  if (filter != ORC_FILTER_BOX && filter != ORC_FILTER_BILINEAR) return -1;
+  if (!isfinite(gx) || !isfinite(gy)) return -1;
+  float r2[ORC_MAX_MIP_LEVELS];
+  for (int i = 0; i < nradii; ++i) {
+    if (!(radii[i] > 0.0f) || !isfinite(radii[i]) || (i > 0 && radii[i] < radii[i - 1])) return -1;
+    r2[i] = radii[i] * radii[i];
+  }
+  float* means[ORC_MAX_MIP_LEVELS] = {0};
+  int64_t wbs[ORC_MAX_MIP_LEVELS], hbs[ORC_MAX_MIP_LEVELS];
+  for (int L = 1; L <= nradii; ++L) {
+    hbs[L] = ceil_shift(h, L);
+    wbs[L] = ceil_shift(w, L);
+    means[L] = (float*)malloc((size_t)(hbs[L] * wbs[L] * 3) * sizeof(float));
+    orc_mip_means(img, pitch, w, h, L, means[L]);
+  }
+  for (int32_t y = 0; y < h; ++y)
+    for (int32_t x = 0; x < w; ++x) {
+      float dx = ((float)x + 0.5f) - gx;
+      float dy = ((float)y + 0.5f) - gy;
+      float d2 = dx * dx + dy * dy;
+      int L = 0;
+      for (int i = 0; i < nradii; ++i) L += d2 > r2[i];
+      float* o = frame + ((int64_t)y * w + x) * 3;
+      if (ring_map) ring_map[(int64_t)y * w + x] = (uint8_t)L;
+      if (L == 0) {
+        for (int c = 0; c < 3; ++c) o[c] = img[(int64_t)y * pitch + 3 * (int64_t)x + c];
+      } else if (filter == ORC_FILTER_BOX) {
+        const float* t = means[L] + (((int64_t)y >> L) * wbs[L] + ((int64_t)x >> L)) * 3;
+        for (int c = 0; c < 3; ++c) o[c] = t[c];
+      } else {
+        int64_t x0, x1, y0, y1;
+        float fx, fy;
+        texel_coord(x, L, wbs[L], &x0, &x1, &fx);
+        texel_coord(y, L, hbs[L], &y0, &y1, &fy);
+        const float* m = means[L];
+        for (int c = 0; c < 3; ++c) {
+          float t00 = m[(y0 * wbs[L] + x0) * 3 + c], t01 = m[(y0 * wbs[L] + x1) * 3 + c];
+          float t10 = m[(y1 * wbs[L] + x0) * 3 + c], t11 = m[(y1 * wbs[L] + x1) * 3 + c];
+          float top = t00 * (1.0f - fx) + t01 * fx;
+          float bot = t10 * (1.0f - fx) + t11 * fx;
+          o[c] = top * (1.0f - fy) + bot * fy;
+        }
+      }
+    }
+  for (int L = 1; L <= nradii; ++L) free(means[L]);
+  return 0;
+}
+
 /* ---------------------------------------------------------------- helpers */
 
 void orc_exp_n(const float* x, float* y, int64_t n) {

@@ -125,6 +125,30 @@ void orc_run_streams(int K, int bias, int64_t n_trials, int n_items, const float
 void orc_chao_literal(int bias, int64_t n_trials, int n_items, const float* w,
                       const float* u, uint32_t* final_idx);
 
+/* Foveation post-process (Sec. 4.3: foveated rendering simulated by a
+ * mip-map of the rendered frame, reconstructed with filtering). */
+#define ORC_MAX_MIP_LEVELS 6
+#define ORC_FILTER_BOX 0
+#define ORC_FILTER_BILINEAR 1
+/* Means of the aligned 2^L x 2^L blocks of an RGB image, [ceil(h/2^L)][ceil(w/2^L)][3].
+ * A block's sum is the quad tree (s00 + s01) + (s10 + s11) of its level-(L-1)
+ * quadrants in FP32, pixels outside the image counting 0; the mean is that
+ * sum / the pixel count, one FP32 division. Pinned: constant images, dyadic
+ * ramps (exact closed forms), FP64 means within the rounding bound. */
+void orc_mip_means(const float* img, int64_t pitch, int32_t w, int32_t h, int32_t L, float* out);
+/* One foveated frame and its ring map. Ring level of pixel (x, y) =
+ * #{i : d2 > r_i * r_i} with dx = ((float)x + 0.5f) - gx, dy likewise,
+ * d2 = dx*dx + dy*dy (FP32, each rounded). Level 0 copies the image; level L
+ * takes the level-L block means, by nearest lookup (box) or bilinear
+ * filtering at u = ((float)x + 0.5f) * 2^-L - 0.5f clamped to the texel
+ * centres, top = t00 (1 - fx) + t01 fx, bot = t10 (1 - fx) + t11 fx,
+ * colour = top (1 - fy) + bot fy. Radii ascending, 1..5 of them. Pinned:
+ * constant image, dyadic ramps, exact ring boundaries, mirror symmetry.
+ * Returns 0, or -1 on bad arguments. */
+int orc_foveate(const float* img, int64_t pitch, int32_t w, int32_t h, int32_t nradii,
+                const float* radii, float gx, float gy, int32_t filter, float* frame,
+                uint8_t* ring_map);
+
 /* Element-wise helpers for tests. */
 void orc_exp_n(const float* x, float* y, int64_t n);
 void orc_log_n(const float* x, float* y, int64_t n);

@@ -17,9 +17,9 @@ scenes and its Tobii recordings, Sec. 5).
 * ``configs``  the five workload shapes (tiny, HD, 4K, 16-stream mix, serving).
 """
 from .configs import WORKLOADS, Workload, StreamSpec, workload
-from .images import ground_truth, box_pyramid
+from .images import bilinear_level, block_counts, block_means, block_sums, box_pyramid, ground_truth
 from .foveate import Foveator, frame_pixels
 from .gaze import gaze_path
 
 __all__ = ["WORKLOADS", "Workload", "StreamSpec", "workload", "ground_truth",
-           "box_pyramid", "Foveator", "frame_pixels", "gaze_path"]
+           "box_pyramid", "block_means", "block_sums", "block_counts", "bilinear_level", "Foveator", "frame_pixels", "gaze_path"]

@@ -570,3 +570,137 @@ def test_full_bias_total_change_flushes(orc):
         assert np.all(b["idx"][:, 0] == 5)
         assert np.all(b["idx"][:, 1:] == orc.EMPTY)
         assert np.array_equal(b["W"], b["wt"][:, 0])
+
+
+# ---------------------------------------------------------------- foveation (Sec. 4.3)
+
+import oracle  # noqa: E402  (built on first use)
+
+def test_foveation_constant_image_is_exact():
+    # every block mean of a constant image is that constant, and both
+    # reconstructions (convex combinations) return it exactly: 0.375 = 3/8
+    # keeps every partial sum and quotient exact in FP32
+    img = np.full((21, 37, 3), 0.375, np.float32)
+    for L in range(1, 6):
+        assert np.all(oracle.mip_means(img, L) == np.float32(0.375))
+    for f in (oracle.FILTER_BOX, oracle.FILTER_BILINEAR):
+        fr, ring = oracle.foveate(img, (3.0, 6.0, 10.0, 14.0, 20.0), 11.0, 9.0, f)
+        assert np.all(fr == np.float32(0.375))
+        assert ring.max() == 5 and ring.min() == 0
+
+
+def _ramp(w, h):
+    img = np.zeros((h, w, 3), np.float32)
+    img[:, :, 0] = (np.arange(w) / 128.0)[None, :]
+    img[:, :, 1] = (np.arange(h) / 64.0)[:, None]
+    img[:, :, 2] = 0.25
+    return img
+
+
+def test_foveation_dyadic_ramp_closed_forms():
+    # block means of a linear ramp are the ramp at the block centre, and
+    # bilinear filtering of block means reproduces a linear ramp wherever no
+    # clamp applies; dyadic values make both exact in FP32
+    w, h = 64, 32
+    img = _ramp(w, h)
+    radii = (0.5, 0.75, 1.0)  # every pixel centre lies beyond all: level 3 everywhere
+    for L in (1, 2, 3):
+        b = 1 << L
+        m = oracle.mip_means(img, L)
+        cx = (np.arange(w // b) * b + (b - 1) / 2.0) / 128.0
+        cy = (np.arange(h // b) * b + (b - 1) / 2.0) / 64.0
+        assert np.array_equal(m[:, :, 0], np.broadcast_to(cx[None, :], m.shape[:2]).astype(np.float32))
+        assert np.array_equal(m[:, :, 1], np.broadcast_to(cy[:, None], m.shape[:2]).astype(np.float32))
+    fr, ring = oracle.foveate(img, radii, -100.0, -100.0, oracle.FILTER_BILINEAR)
+    assert np.all(ring == 3)
+    inner = (slice(4, h - 4), slice(4, w - 4))
+    assert np.array_equal(fr[inner], img[inner])
+    fb, _ = oracle.foveate(img, radii, -100.0, -100.0, oracle.FILTER_BOX)
+    m3 = oracle.mip_means(img, 3)
+    assert np.array_equal(fb, np.repeat(np.repeat(m3, 8, 0), 8, 1))
+
+
+def test_foveation_bilinear_texel_centre_weights():
+    # textbook bilinear magnification by 2 with texel-centre sampling and
+    # clamp-to-edge: level-1 means [0, 1] give pixel colours [0, 1/4, 3/4, 1]
+    img = np.zeros((2, 4, 3), np.float32)
+    img[:, 2:] = 1.0
+    fr, ring = oracle.foveate(img, (0.25,), -50.0, -50.0, oracle.FILTER_BILINEAR)
+    assert np.all(ring == 1)
+    assert np.array_equal(fr[0, :, 0], np.array([0.0, 0.25, 0.75, 1.0], np.float32))
+    # and vertically: a [0; 1] column of level-1 means
+    img = np.zeros((4, 2, 3), np.float32)
+    img[2:] = 1.0
+    fr, _ = oracle.foveate(img, (0.25,), -50.0, -50.0, oracle.FILTER_BILINEAR)
+    assert np.array_equal(fr[:, 0, 1], np.array([0.0, 0.25, 0.75, 1.0], np.float32))
+
+
+def test_foveation_ring_boundaries_exact():
+    from fractions import Fraction as Fr
+    w, h = 24, 18
+    gx, gy = 10.25, 7.5
+    radii = (2.5, 5.0, 7.75)
+    img = np.zeros((h, w, 3), np.float32)
+    _, ring = oracle.foveate(img, radii, gx, gy, oracle.FILTER_BOX)
+    on_boundary = 0
+    for y in range(h):
+        for x in range(w):
+            d2 = (Fr(2 * x + 1, 2) - Fr(gx)) ** 2 + (Fr(2 * y + 1, 2) - Fr(gy)) ** 2
+            expect = sum(d2 > Fr(r) ** 2 for r in radii)
+            on_boundary += any(d2 == Fr(r) ** 2 for r in radii)
+            assert ring[y, x] == expect, (x, y)
+    assert on_boundary > 0  # the inclusive boundary case is exercised
+
+
+def test_foveation_mirror_symmetry():
+    # mirroring the image and the gaze mirrors the output exactly (widths are
+    # multiples of the largest block, so blocks map onto blocks; addition is
+    # commutative and the bilinear weights swap): catches swapped weights or
+    # a wrong neighbour index
+    from synth import ground_truth
+    w, h = 64, 40
+    img = ground_truth(w, h, seed=8)
+    radii = (5.0, 11.0, 17.0)
+    gx, gy = 23.25, 14.5
+    for f in (oracle.FILTER_BOX, oracle.FILTER_BILINEAR):
+        a, ra = oracle.foveate(img, radii, gx, gy, f)
+        b, rb = oracle.foveate(np.ascontiguousarray(img[:, ::-1]), radii, w - gx, gy, f)
+        assert np.array_equal(ra, rb[:, ::-1])
+        assert np.array_equal(a, b[:, ::-1])
+        c, rc = oracle.foveate(np.ascontiguousarray(img[::-1]), radii, gx, h - gy, f)
+        assert np.array_equal(ra, rc[::-1])
+        assert np.array_equal(a, c[::-1])
+
+
+def test_foveation_means_within_rounding_of_fp64():
+    rng = np.random.default_rng(3)
+    img = rng.random((45, 70, 3)).astype(np.float32)
+    for L in range(1, 6):
+        b = 1 << L
+        m = oracle.mip_means(img, L)
+        for by in range(m.shape[0]):
+            for bx in range(m.shape[1]):
+                ref = img[by * b:(by + 1) * b, bx * b:(bx + 1) * b].astype(np.float64).mean(axis=(0, 1))
+                # 2L tree additions and one division, each within 2^-24 relative
+                assert np.all(np.abs(m[by, bx] - ref) <= (2 * L + 1) * 2.0 ** -24 * ref + 1e-30)
+
+
+def test_foveation_rejects_bad_arguments():
+    img = np.zeros((4, 4, 3), np.float32)
+    for radii in ((), (2.0, 1.0), (1.0,) * 6, (0.0,), (float("nan"),)):
+        with pytest.raises(ValueError):
+            oracle.foveate(img, radii, 1.0, 1.0)
+    with pytest.raises(ValueError):
+        oracle.foveate(img, (1.0,), 1.0, 1.0, filter=2)
+
+
+def test_foveation_matches_the_input_generator():
+    # the seeded input generator (numpy/torch) and the oracle (C loops) are
+    # written separately from the same definition
+    from synth import Foveator
+    radii = (4.0, 9.0, 15.0)
+    for name, f in (("box", oracle.FILTER_BOX), ("bilinear", oracle.FILTER_BILINEAR)):
+        fv = Foveator(53, 29, radii, seed=6, filter=name)
+        a, ra = oracle.foveate(fv.gt_numpy, radii, 20.3, 11.7, f)
+        b, rb = fv.frame(20.3, 11.7)
+        assert np.array_equal(ra, rb.numpy()) and np.array_equal(a, b.numpy())

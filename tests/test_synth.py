@@ -38,8 +38,9 @@ def test_foveated_frame_rings():
     assert np.array_equal(fr.numpy().reshape(-1, 3), ref[0])
 
 
-def test_foveator_float64_path_is_exact_across_devices():
-    # the ring test uses float64 sub/mul/add only; check it against exact rationals
+def test_foveator_ring_test_is_exact_on_dyadic_inputs():
+    # the ring test uses float32 sub/mul/add only; with dyadic gaze and radius
+    # every step is exact, so it must agree with exact rationals
     fv = Foveator(16, 16, (3.0,), seed=0)
     lev = fv.ring_map(7.75, 8.5).numpy()
     for y in range(16):
@@ -47,6 +48,30 @@ def test_foveator_float64_path_is_exact_across_devices():
             dx, dy = x + 0.5 - 7.75, y + 0.5 - 8.5
             assert lev[y, x] == (dx * dx + dy * dy > 9.0)
     assert torch.equal(fv.ring_map(7.75, 8.5), fv.ring_map(7.75, 8.5))
+    # the boundary is inclusive: d2 == r2 stays inside (pixel (10, 8): dx = 2.75, dy = 0)
+    fv2 = Foveator(16, 16, (2.75,), seed=0)
+    assert fv2.ring_map(7.75, 8.5).numpy()[8, 10] == 0
+    assert fv2.ring_map(7.75, 8.5).numpy()[8, 11] == 1
+
+
+def test_block_sums_tree_and_counts():
+    from synth import block_counts, block_sums
+    img = ground_truth(37, 21, seed=5)
+    for lev in (1, 2, 3, 4):
+        s = block_sums(img, lev)
+        b = 1 << lev
+        # the tree sum is within float32 rounding of the FP64 block sum
+        for (i, j) in ((0, 0), (s.shape[0] - 1, s.shape[1] - 1), (1, 2)):
+            ref = img[i * b:(i + 1) * b, j * b:(j + 1) * b].astype(np.float64).sum(axis=(0, 1))
+            assert np.allclose(s[i, j], ref, rtol=lev * 2.0 ** -23, atol=0)
+        n = block_counts(21, 37, lev)
+        assert n.sum() == 21 * 37
+    # level L+1 sums are the quad sums of level L sums, in the stated order
+    s1, s2 = block_sums(img, 1), block_sums(img, 2)
+    pad = np.zeros((2 * s2.shape[0], 2 * s2.shape[1], 3), np.float32)
+    pad[:s1.shape[0], :s1.shape[1]] = s1
+    quad = (pad[0::2, 0::2] + pad[0::2, 1::2]) + (pad[1::2, 0::2] + pad[1::2, 1::2])
+    assert np.array_equal(quad, s2)
 
 
 def test_gaze_paths():
@@ -69,3 +94,34 @@ def test_workloads():
     assert len(mix.streams) == 16 and mix.pixels == 68917248
     assert [s.K for s in mix.streams[:4]] == [8, 4, 8, 4]
     assert all(s.color_fp16 for s in mix.streams)
+
+
+def test_block_means_order_and_bilinear():
+    from synth import bilinear_level, block_means
+    img = ground_truth(37, 21, seed=3)
+    for lev in (1, 2, 3):
+        m = block_means(img, lev)
+        b = 1 << lev
+        assert m.shape == (-(-21 // b), -(-37 // b), 3)
+        blk = img[b:2 * b, 0:b].astype(np.float64).mean(axis=(0, 1))
+        assert np.allclose(m[1, 0], blk, atol=1e-6)
+        bl = bilinear_level(m, lev, 21, 37)
+        # convex weights: the reconstruction stays within the range of the means
+        assert bl.min() >= m.min() - 1e-6 and bl.max() <= m.max() + 1e-6
+    # a linear ramp is reproduced exactly by block means + bilinear filtering
+    # wherever no clamp applies (closed form: the mean of a block is the ramp
+    # at the block centre, and bilinear interpolation of a linear function is
+    # that function)
+    w, h = 64, 32
+    ramp = np.zeros((h, w, 3), np.float32)
+    ramp[:, :, 0] = (np.arange(w) / 128.0)[None, :]
+    ramp[:, :, 1] = (np.arange(h) / 64.0)[:, None]
+    for lev in (1, 2, 3):
+        b = 1 << lev
+        bl = bilinear_level(block_means(ramp, lev), lev, h, w)
+        inner = slice(b, -b)
+        assert np.allclose(bl[inner, inner], ramp[inner, inner], atol=1e-6)
+        assert np.all(bl[:, :, 2] == 0.0)
+    fv = Foveator(37, 21, (4.0, 9.0), seed=3, filter="bilinear")
+    fr, lev = fv.frame(10.0, 10.0)
+    assert fr.shape == (21, 37, 3) and np.all(fr.numpy() >= 0) and np.all(fr.numpy() <= 1)
