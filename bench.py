@@ -316,6 +316,112 @@ def run_batched(args, dev):
                        "tile_px": 256 * tuned["batch"][0], "chosen_by": "autotune.tune_batch"}}
 
 
+def _timed_flushed(fn, reps: int, stream, flush: torch.Tensor) -> list:
+    """Per-call device times (ms) with the L2 flushed (a write larger than L2)
+    before every call, outside the timed region."""
+    times = []
+    for _ in range(3):
+        fn()
+    for _ in range(reps):
+        flush.add_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    return times
+
+
+def run_foveation(args, dev, spec, seed, gaze):
+    """The foveation post-process (Sec. 4.3) on the device at the workload's size:
+    the mip build (once per rendered image), one foveated frame + ring map per
+    gaze (box and bilinear), and the GPU-resident frame loop
+    foveate -> push -> fused resolve."""
+    import paper_2510_03964_gb300 as wrs
+    from synth import ground_truth
+    stream = torch.cuda.Stream(device=dev)
+    img = torch.from_numpy(ground_truth(spec.width, spec.height, seed)).to(dev)
+    hw = spec.width * spec.height
+    levels = len(spec.radii) + 1
+    lay = wrs.mip_layout(spec.width, spec.height, levels)
+    texels = [lay.width[L] * lay.height[L] for L in range(1, levels)]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    reps = args.fov_reps
+    peaks = measured_peaks()
+    out = {"image": f"{spec.width}x{spec.height} RGB f32, {levels} levels, radii {list(spec.radii)}",
+           "timing": f"median of {reps} calls, CUDA events on the launching stream, L2 flushed "
+                     f"(256 MB write) before each call"}
+    with torch.cuda.stream(stream):
+        mip = wrs.mip_build(img, levels, stream=stream)
+        t_mip = _timed_flushed(lambda: wrs.mip_build(img, levels, out=mip, stream=stream), reps, stream, flush)
+        mip_ms = statistics.median(t_mip)
+        mip_bytes = hw * 12 + 16 * sum(texels)
+        out["mip_build"] = {"ms": round(mip_ms, 4), "algorithmic_bytes": mip_bytes,
+                            "gbs": round(mip_bytes / (mip_ms * 1e-3) / 1e9, 1),
+                            "frac": round(mip_bytes / (mip_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                            "bytes_rule": "image read 12 B/px + every texel of levels >= 1 written once (16 B)"}
+        frame = torch.empty((spec.height, spec.width, 3), dtype=torch.float32, device=dev)
+        ring = torch.empty((spec.height, spec.width), dtype=torch.uint8, device=dev)
+        gi = [0]
+
+        for name in ("box", "bilinear"):
+            def call(name=name):
+                g = gaze[gi[0] % len(gaze)]
+                gi[0] += 1
+                wrs.foveate(img, mip, spec.radii, g, name, out=frame, ring_map=ring, stream=stream)
+            t = _timed_flushed(call, reps, stream, flush)
+            ms = statistics.median(t)
+            # algorithmic bytes of the last call: frame + ring written, fovea pixels
+            # read from the image, each texel of the levels in use read once
+            lev_hist = torch.bincount(ring.reshape(-1).to(torch.int64), minlength=levels).cpu().tolist()
+            used = sum(16 * texels[L - 1] for L in range(1, levels) if lev_hist[L] > 0)
+            nbytes = hw * 13 + 12 * lev_hist[0] + used
+            gbs = nbytes / (ms * 1e-3) / 1e9
+            out[f"foveate_{name}"] = {
+                "ms": round(ms, 4), "algorithmic_bytes": int(nbytes), "gbs": round(gbs, 1),
+                "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"],
+                             "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4)},
+                "bytes_rule": "frame 12 B/px + ring map 1 B/px written, 12 B per fovea pixel read, "
+                              "16 B per texel of each level in use read once",
+                "pixels_per_level": lev_hist}
+
+        # GPU-resident frame loop: foveate (bilinear) -> push with fused resolve
+        res = torch.empty_like(frame)
+        st = wrs.Stream(spec.width, spec.height, spec.K, spec.r_f, seed=seed, stream_id=spec.stream_id,
+                        color_fp16=spec.color_fp16, temporal_bias=spec.temporal_bias, device=dev,
+                        stream=stream, update_rule=spec.update_rule)
+        n_loop = args.fov_loop_frames
+
+        def step(t):
+            g = gaze[t % len(gaze)]
+            wrs.foveate(img, mip, spec.radii, g, "bilinear", out=frame, ring_map=ring, stream=stream)
+            st.push_frame(frame, g, ring, res, stream=stream)
+
+        for t in range(5):
+            step(t)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n_loop)]
+        for t in range(n_loop):
+            g = gaze[(5 + t) % len(gaze)]
+            ev[t][0].record(stream)
+            wrs.foveate(img, mip, spec.radii, g, "bilinear", out=frame, ring_map=ring, stream=stream)
+            ev[t][1].record(stream)
+            st.push_frame(frame, g, ring, res, stream=stream)
+            ev[t][2].record(stream)
+        ev[-1][2].synchronize()
+        total = ev[0][0].elapsed_time(ev[-1][2])
+        fov_ms = statistics.median(e[0].elapsed_time(e[1]) for e in ev)
+        push_ms = statistics.median(e[1].elapsed_time(e[2]) for e in ev)
+        out["loop_foveate_push_resolve"] = {
+            "ms_per_frame": round(total / n_loop, 4), "frames": n_loop,
+            "foveate_ms_median": round(fov_ms, 4), "push_ms_median": round(push_ms, 4),
+            "note": "per frame: wrs_foveate (bilinear, ring map) then wrs_push_frame with the ring "
+                    "map and fused resolve, back to back on one stream, no flush (the real-time loop)"}
+        st.close()
+    del flush
+    return out
+
+
 def run_serving(args, dev):
     """The 64-viewer serving trace at the workload's frame rates (72-120 Hz per
     viewer) and at an overload (200-300 Hz), batched vs one launch per frame."""
@@ -434,6 +540,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.empty_cache()
     batched = run_batched(args, dev) if args.batch_rounds > 0 else None
     torch.cuda.empty_cache()
+    foveation = run_foveation(args, dev, spec, seed, gaze) if args.fov_reps > 0 else None
+    torch.cuda.empty_cache()
     serving = run_serving(args, dev) if args.serve > 0 else None
     torch.cuda.empty_cache()
 
@@ -475,6 +583,7 @@ def run_ours(args, world, rank, local):
         "clocks": clk,
         "e2e": e2e,
         "batched": batched,
+        "foveation": foveation,
         "serving": serving,
     }
     if args.cpu_baseline:
@@ -513,6 +622,9 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=65536)
     ap.add_argument("--batch-rounds", type=int, default=100,
                     help="rounds of the 16-stream batched workload (0 skips it)")
+    ap.add_argument("--fov-reps", type=int, default=50,
+                    help="timed calls of each foveation kernel (0 skips the foveation section)")
+    ap.add_argument("--fov-loop-frames", type=int, default=200)
     ap.add_argument("--serve", type=float, default=8.0,
                     help="seconds of the 64-viewer serving trace per mode and load (0 skips it)")
     args = ap.parse_args()

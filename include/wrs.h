@@ -238,6 +238,72 @@ int wrs_push_batch(wrs_batch* batch, int n, wrs_ctx* const* ctxs, const float* c
  * frame). Waits for `stream`. */
 int wrs_get_stats(wrs_ctx* ctx, uint64_t* replacements, wrs_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Foveation post-process (Sec. 4.3, "Implementation"): the paper simulates
+ * foveated rendering on the rendered frame by mip-mapping it and
+ * reconstructing each ring around the gaze from a coarser level with
+ * filtering. These calls produce, on the device, the foveated frames and
+ * ring maps that wrs_push_frame consumes, from a full-resolution image.
+ * ------------------------------------------------------------------------ */
+#define WRS_MAX_MIP_LEVELS 6   /* level 0 (the image) .. level 5 (32 x 32 blocks) */
+#define WRS_FILTER_BOX 0       /* nearest lookup of the level's block mean */
+#define WRS_FILTER_BILINEAR 1  /* bilinear filtering of the level's block means */
+
+/* Where each level of a mip buffer lives. Level L >= 1 holds one texel per
+ * aligned 2^L x 2^L block of the image, [height[L]][width[L]] texels of
+ * 16 bytes {r, g, b, 0} (float), row-major from offset[L]; offsets are
+ * 256-byte aligned. Level 0 is the image itself (offset[0] = -1). */
+typedef struct {
+  int32_t levels;                        /* levels described, 1..WRS_MAX_MIP_LEVELS */
+  int32_t width[WRS_MAX_MIP_LEVELS];     /* ceil(image width / 2^L) */
+  int32_t height[WRS_MAX_MIP_LEVELS];    /* ceil(image height / 2^L) */
+  int64_t offset[WRS_MAX_MIP_LEVELS];    /* byte offset of level L; -1 for level 0 */
+  int64_t total_bytes;                   /* bytes the buffer must hold (0 when levels = 1) */
+} wrs_mip_layout;
+
+/* Layout of the mip buffer of a width x height image with `levels` levels
+ * (levels 1..L-1 are stored). Levels 1..n of a buffer laid out for more levels
+ * sit at the same offsets as in one laid out for n + 1 levels.
+ * Returns WRS_ERR_ARG for sizes < 1, width * height >= 2^31 or levels outside
+ * 1..WRS_MAX_MIP_LEVELS. */
+int wrs_mip_layout_get(int32_t width, int32_t height, int32_t levels, wrs_mip_layout* out);
+
+/* Builds levels 1..levels-1 of the mip buffer from an RGB float image
+ * [height][img_pitch_elems] (RGB triples, pitch >= 3 * width, 4-byte aligned).
+ * Texel = the block's mean: the FP32 sum over the block, formed as the quad
+ * tree (s00 + s01) + (s10 + s11) of its four half-size quadrants (pixels
+ * outside the image count as 0), divided by the number of image pixels in the
+ * block. d_mip: caller-owned device buffer of at least the layout's
+ * total_bytes, 256-byte aligned. Asynchronous on `stream`; the image must not
+ * change until the call completes. Errors: WRS_ERR_ARG (NULL or unaligned
+ * pointers, bad sizes), WRS_ERR_BUDGET (buffer too small), WRS_ERR_CUDA. */
+int wrs_mip_build(const float* d_img, int64_t img_pitch_elems, int32_t width, int32_t height,
+                  int32_t levels, void* d_mip, size_t mip_bytes, wrs_stream_t stream);
+
+/* One foveated frame for the gaze (gaze_x, gaze_y) in pixels.
+ * Ring level of pixel (x, y): the number of radii r_i with
+ * dx*dx + dy*dy > r_i*r_i, dx = (x + 0.5) - gaze_x, dy likewise, all FP32
+ * rounded once (a centre exactly on a radius stays inside it). radii: host
+ * array of nradii (1..WRS_MAX_MIP_LEVELS-1) finite positive values in
+ * ascending order; radii[0] is the foveal radius. Level 0 copies the image
+ * pixel; level L reads the level-L texels of d_mip (built by wrs_mip_build
+ * with at least nradii + 1 levels; mip_bytes its size): WRS_FILTER_BOX takes
+ * the texel of the pixel's block; WRS_FILTER_BILINEAR samples at the level
+ * coordinate u = (x + 0.5) * 2^-L - 0.5 (v likewise) clamped to
+ * [0, width[L] - 1], with x0 = floor(u), fx = u - x0, x1 = min(x0 + 1,
+ * width[L] - 1) and colour = top * (1 - fy) + bot * fy,
+ * top = t00 * (1 - fx) + t01 * fx, bot = t10 * (1 - fx) + t11 * fx, each
+ * product and sum one FP32 rounding. Writes d_frame [height][frame_pitch_elems]
+ * (RGB triples) and, if d_ring_map is not NULL, the level of each pixel to
+ * d_ring_map [height][width] (bytes 0..nradii: a valid fov map for
+ * wrs_push_frame, no flushes). d_img and d_frame must not overlap.
+ * Asynchronous on `stream`. Errors: WRS_ERR_ARG, WRS_ERR_BUDGET (mip_bytes
+ * below the layout's size for nradii + 1 levels), WRS_ERR_CUDA. */
+int wrs_foveate(const float* d_img, int64_t img_pitch_elems, const void* d_mip, size_t mip_bytes,
+                int32_t width, int32_t height, int32_t nradii, const float* radii, float gaze_x,
+                float gaze_y, int32_t filter, float* d_frame, int64_t frame_pitch_elems,
+                uint8_t* d_ring_map, wrs_stream_t stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* wrs_last_error(void);
 

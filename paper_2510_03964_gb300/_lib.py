@@ -30,6 +30,16 @@ class WrsLayout(C.Structure):
                 ("col_off", C.c_int64), ("total_bytes", C.c_int64)]
 
 
+WRS_MAX_MIP_LEVELS = 6
+WRS_FILTER_BOX, WRS_FILTER_BILINEAR = 0, 1
+
+
+class WrsMipLayout(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("width", C.c_int32 * WRS_MAX_MIP_LEVELS),
+                ("height", C.c_int32 * WRS_MAX_MIP_LEVELS), ("offset", C.c_int64 * WRS_MAX_MIP_LEVELS),
+                ("total_bytes", C.c_int64)]
+
+
 _V = C.c_void_p
 _I = C.c_int
 SIGNATURES = {
@@ -55,6 +65,10 @@ SIGNATURES = {
     "wrs_batch_get_launch": (_I, [_V, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "wrs_push_batch": (_I, [_V, _I, _V, _V, _V, _V, _V, _V]),
     "wrs_get_stats": (_I, [_V, C.POINTER(C.c_uint64), _V]),
+    "wrs_mip_layout_get": (_I, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(WrsMipLayout)]),
+    "wrs_mip_build": (_I, [_V, C.c_int64, C.c_int32, C.c_int32, C.c_int32, _V, C.c_size_t, _V]),
+    "wrs_foveate": (_I, [_V, C.c_int64, _V, C.c_size_t, C.c_int32, C.c_int32, C.c_int32, _V,
+                         C.c_float, C.c_float, C.c_int32, _V, C.c_int64, _V, _V]),
     "wrs_last_error": (C.c_char_p, []),
 }
 

@@ -10,7 +10,8 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import (WRS_EMPTY_SLOT, WrsConfig, WrsError, WrsLayout, check, load)
+from ._lib import (WRS_EMPTY_SLOT, WRS_FILTER_BILINEAR, WRS_FILTER_BOX, WrsConfig, WrsError,
+                   WrsLayout, WrsMipLayout, check, load)
 
 
 def _stream_handle(stream) -> int:
@@ -252,3 +253,91 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------ foveation post-process
+
+FILTERS = {"box": WRS_FILTER_BOX, "bilinear": WRS_FILTER_BILINEAR}
+
+
+def mip_layout(width: int, height: int, levels: int) -> WrsMipLayout:
+    lay = WrsMipLayout()
+    check(load().wrs_mip_layout_get(int(width), int(height), int(levels), C.byref(lay)))
+    return lay
+
+
+def _image_args(img: torch.Tensor, name: str):
+    if img.dim() != 3 or img.shape[2] != 3 or img.stride(2) != 1 or img.stride(1) != 3:
+        raise ValueError(f"{name} must be a [H][W][3] float32 tensor with packed pixels")
+    return _dev_ptr(img, torch.float32, name), int(img.stride(0))
+
+
+def mip_build(img: torch.Tensor, levels: int, out: torch.Tensor | None = None,
+              stream=None) -> torch.Tensor:
+    """Levels 1..levels-1 of the mip buffer of ``img`` ([H][W][3] float32 on
+    the GPU) into ``out`` (uint8, allocated if None)."""
+    h, w = int(img.shape[0]), int(img.shape[1])
+    lay = mip_layout(w, h, levels)
+    if out is None:
+        out = torch.empty(max(int(lay.total_bytes), 256), dtype=torch.uint8, device=img.device)
+    ptr, pitch = _image_args(img, "img")
+    with torch.cuda.device(img.device):
+        check(load().wrs_mip_build(ptr, pitch, w, h, int(levels), _dev_ptr(out, torch.uint8, "mip"),
+                                   out.numel(), _stream_handle(stream)))
+    return out
+
+
+def mip_levels(mip: torch.Tensor, width: int, height: int, levels: int) -> list:
+    """Views [height[L]][width[L]][4] float32 of levels 1..levels-1 of a mip buffer."""
+    lay = mip_layout(width, height, levels)
+    out = []
+    for L in range(1, levels):
+        n = lay.width[L] * lay.height[L] * 16
+        out.append(mip[lay.offset[L]:lay.offset[L] + n].view(torch.float32)
+                   .view(lay.height[L], lay.width[L], 4))
+    return out
+
+
+def foveate(img: torch.Tensor, mip: torch.Tensor, radii, gaze, filter="box",
+            out: torch.Tensor | None = None, ring_map: torch.Tensor | None = None,
+            want_ring_map: bool = True, stream=None):
+    """(frame [H][W][3] float32, ring map [H][W] uint8 or None) of the
+    foveation post-process for one gaze; ``mip`` from mip_build with at least
+    len(radii) + 1 levels."""
+    h, w = int(img.shape[0]), int(img.shape[1])
+    if out is None:
+        out = torch.empty((h, w, 3), dtype=torch.float32, device=img.device)
+    if ring_map is None and want_ring_map:
+        ring_map = torch.empty((h, w), dtype=torch.uint8, device=img.device)
+    if ring_map is not None and (tuple(ring_map.shape) != (h, w) or not ring_map.is_contiguous()):
+        raise ValueError("ring_map must be a contiguous [H][W] uint8 tensor")
+    r = (C.c_float * len(radii))(*[float(v) for v in radii])
+    iptr, ipitch = _image_args(img, "img")
+    optr, opitch = _image_args(out, "out")
+    f = FILTERS[filter] if isinstance(filter, str) else int(filter)
+    with torch.cuda.device(img.device):
+        check(load().wrs_foveate(iptr, ipitch, _dev_ptr(mip, torch.uint8, "mip"), mip.numel(), w, h,
+                                 len(radii), r, float(gaze[0]), float(gaze[1]), f, optr, opitch,
+                                 _dev_ptr(ring_map, torch.uint8, "ring_map"), _stream_handle(stream)))
+    return out, ring_map
+
+
+class Foveation:
+    """A rendered full-resolution image and its mip buffer, resident on the
+    GPU, producing foveated frames for any gaze (Sec. 4.3)."""
+
+    def __init__(self, img: torch.Tensor, radii, filter="box", stream=None):
+        self.img = img
+        self.radii = tuple(float(r) for r in radii)
+        self.levels = len(self.radii) + 1
+        self.filter = filter
+        self.height, self.width = int(img.shape[0]), int(img.shape[1])
+        self.mip = mip_build(img, self.levels, stream=stream)
+
+    def rebuild(self, stream=None):
+        """Re-derive the mip levels after the image changed (a new rendered frame)."""
+        mip_build(self.img, self.levels, out=self.mip, stream=stream)
+
+    def frame(self, gaze, out=None, ring_map=None, want_ring_map=True, stream=None):
+        return foveate(self.img, self.mip, self.radii, gaze, self.filter, out, ring_map,
+                       want_ring_map, stream)

@@ -84,3 +84,48 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.wrs_destroy(None) == _lib.WRS_OK
     assert lib.wrs_frame_index(None) == 0
     assert lib.wrs_set_launch(None, 128, 4) == _lib.WRS_ERR_ARG
+
+
+def test_mip_layout(lib):
+    lay = pkg.mip_layout(3840, 2160, 4)
+    assert lay.levels == 4 and lay.offset[0] == -1
+    assert [lay.width[L] for L in range(4)] == [3840, 1920, 960, 480]
+    assert [lay.height[L] for L in range(4)] == [2160, 1080, 540, 270]
+    off = 0
+    for L in range(1, 4):
+        assert lay.offset[L] == off and off % 256 == 0
+        off += -(-lay.width[L] * lay.height[L] * 16 // 256) * 256
+    assert lay.total_bytes == off
+    # ragged sizes round up; levels of a deeper layout sit at the same offsets
+    lay6 = pkg.mip_layout(37, 21, 6)
+    assert [lay6.width[L] for L in range(6)] == [37, 19, 10, 5, 3, 2]
+    assert [lay6.height[L] for L in range(6)] == [21, 11, 6, 3, 2, 1]
+    lay3 = pkg.mip_layout(37, 21, 3)
+    assert list(lay3.offset)[:3] == list(lay6.offset)[:3]
+    assert pkg.mip_layout(5, 5, 1).total_bytes == 0
+    for bad in ((0, 5, 2), (5, 5, 0), (5, 5, 7), (1 << 16, 1 << 15, 2)):
+        with pytest.raises(pkg.WrsError):
+            pkg.mip_layout(*bad)
+
+
+def test_foveate_host_checks_before_any_cuda_call(lib):
+    # every failure below is decided on the host from the arguments alone;
+    # the pointers are never dereferenced
+    fake = C.c_void_p(1 << 20)
+    r = (C.c_float * 2)(2.0, 1.0)
+    assert lib.wrs_foveate(fake, 48, fake, 4096, 16, 8, 2, r, 8.0, 4.0, 0, fake, 48, None,
+                           None) == _lib.WRS_ERR_ARG
+    assert b"ascending" in lib.wrs_last_error()
+    r = (C.c_float * 1)(2.0)
+    assert lib.wrs_foveate(fake, 48, fake, 4096, 16, 8, 1, r, 8.0, 4.0, 2, fake, 48, None,
+                           None) == _lib.WRS_ERR_ARG
+    assert lib.wrs_foveate(fake, 47, fake, 4096, 16, 8, 1, r, 8.0, 4.0, 0, fake, 48, None,
+                           None) == _lib.WRS_ERR_ARG
+    assert lib.wrs_foveate(fake, 48, fake, 16, 16, 8, 1, r, 8.0, 4.0, 0, fake, 48, None,
+                           None) == _lib.WRS_ERR_BUDGET
+    assert lib.wrs_foveate(fake, 48, fake, 4096, 16, 8, 0, r, 8.0, 4.0, 0, fake, 48, None,
+                           None) == _lib.WRS_ERR_ARG
+    assert lib.wrs_mip_build(fake, 48, 16, 8, 3, fake, 16, None) == _lib.WRS_ERR_BUDGET
+    assert lib.wrs_mip_build(None, 48, 16, 8, 3, fake, 4096, None) == _lib.WRS_ERR_ARG
+    assert lib.wrs_mip_build(fake, 48, 16, 8, 3, C.c_void_p((1 << 20) + 16), 4096,
+                             None) == _lib.WRS_ERR_ARG
