@@ -86,6 +86,10 @@ def load():
                 "orc_weight32_grid": (None, [C.POINTER(Config), C.c_float, C.c_float, _P]),
                 "orc_lightness": (C.c_float, [C.c_float, C.c_float, C.c_float]),
                 "orc_lightness_n": (None, [_P, _P, C.c_int64]),
+                "orc_push_frame_reproject": (C.c_int, [C.POINTER(Config), C.c_uint32, _P, C.c_int64,
+                                                       C.c_float, C.c_float, _P, _P, _P, C.c_float, _P,
+                                                       _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                                       C.c_int]),
                 "orc_mip_means": (None, [_P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, _P]),
                 "orc_foveate": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, _P,
                                           C.c_float, C.c_float, C.c_int32, _P, _P]),
@@ -278,6 +282,33 @@ class OracleStream:
                                    _ptr(self.wt), _ptr(self.rgb), self.nthreads)
         if rc != 0:
             raise ValueError("oracle rejected the frame arguments")
+        self.t += 1
+
+    def push_frame_reproject(self, frame: np.ndarray, gaze, motion: np.ndarray | None = None,
+                             depth: np.ndarray | None = None, prev_depth: np.ndarray | None = None,
+                             depth_tol: float = 0.05, fov_map: np.ndarray | None = None):
+        """One frame with temporal reprojection (see orc_push_frame_reproject);
+        the stream must hold every pixel."""
+        if self.pixels is not None:
+            raise ValueError("reprojection gathers from the whole previous frame: no pixel sample")
+        frame = np.ascontiguousarray(frame, dtype=np.float32)
+        mv = None if motion is None else np.ascontiguousarray(motion, dtype=np.float32)
+        d = None if depth is None else _f32(depth)
+        dp = None if prev_depth is None else _f32(prev_depth)
+        fm = None if fov_map is None else np.ascontiguousarray(fov_map, dtype=np.uint8)
+        nxt = {k: np.empty_like(v) for k, v in
+               (("W", self.W), ("P", self.P), ("key", self.key), ("idx", self.idx),
+                ("wt", self.wt), ("rgb", self.rgb))}
+        rc = load().orc_push_frame_reproject(
+            C.byref(self.cfg), self.t, _ptr(frame), 3 * self.cfg.width, float(gaze[0]),
+            float(gaze[1]), _ptr(mv), _ptr(d), _ptr(dp), float(depth_tol), _ptr(fm),
+            _ptr(self.W), _ptr(self.P), _ptr(self.key), _ptr(self.idx), _ptr(self.wt),
+            _ptr(self.rgb), _ptr(nxt["W"]), _ptr(nxt["P"]), _ptr(nxt["key"]), _ptr(nxt["idx"]),
+            _ptr(nxt["wt"]), _ptr(nxt["rgb"]), self.nthreads)
+        if rc != 0:
+            raise ValueError("oracle rejected the frame arguments")
+        self.W, self.P, self.key, self.idx = nxt["W"], nxt["P"], nxt["key"], nxt["idx"]
+        self.wt, self.rgb = nxt["wt"], nxt["rgb"]
         self.t += 1
 
     def resolve(self) -> np.ndarray:

@@ -508,6 +508,100 @@ void orc_resolve(int K, int64_t npix, const uint32_t* idx, const float* wt, cons
   for (int k = 0; k < nthreads; ++k) pthread_join(th[k], NULL);
 }
 
+/* ---------------------------------------------------------------- reprojection */
+
+typedef struct {
+  orc_job base;
+  const float *motion, *depth, *prev_depth;
+  float tol;
+  const float *W0, *P0, *key0, *wt0, *rgb0;
+  const uint32_t* idx0;
+} orc_rpjob;
+
+static void* reproject_thread(void* arg) {
+  orc_rpjob* r = (orc_rpjob*)arg;
+  orc_job* j = &r->base;
+  const orc_config* c = j->cfg;
+  const int K = c->K;
+  for (int64_t p = j->i0; p < j->i1; ++p) {
+    int32_t x = (int32_t)(p % c->width), y = (int32_t)(p / c->width);
+    float mx = r->motion ? r->motion[2 * p] : 0.0f;
+    float my = r->motion ? r->motion[2 * p + 1] : 0.0f;
+    float cx = ((float)x + 0.5f) - mx;
+    float cy = ((float)y + 0.5f) - my;
+    int valid = cx >= 0.0f && cx < (float)c->width && cy >= 0.0f && cy < (float)c->height;
+    int64_t q = p;
+    if (valid) q = (int64_t)floorf(cy) * c->width + (int64_t)floorf(cx);
+    if (valid && r->depth) {
+      float dp = r->depth[p], dq = r->prev_depth[q];
+      if (fabsf(dq - dp) > r->tol * dp) valid = 0;
+    }
+    /* the history of p is the previous reservoir at q */
+    j->W[p] = r->W0[q];
+    j->P[p] = r->P0[q];
+    for (int s = 0; s < K; ++s) {
+      j->key[p * K + s] = r->key0[q * K + s];
+      j->idx[p * K + s] = r->idx0[q * K + s];
+      j->wt[p * K + s] = r->wt0[q * K + s];
+      for (int ch = 0; ch < 3; ++ch) j->rgb[(p * K + s) * 3 + ch] = r->rgb0[(q * K + s) * 3 + ch];
+    }
+    float w = orc_weight32(c, x, y, j->gx, j->gy);
+    float u = orc_uniform(c->seed, c->stream_id, j->t, p);
+    const float* src = j->frame + (int64_t)y * j->pitch + 3 * (int64_t)x;
+    int flush = !valid || (j->fov_map ? (j->fov_map[p] == 0xFF) : 0);
+    if (c->rule == 1)
+      orc_pixel_step_literal_full(c->temporal_bias, c->color_fp16, w, u, j->t, src, flush,
+                                  &j->W[p], &j->idx[p], &j->wt[p], &j->rgb[p * 3]);
+    else
+      orc_pixel_step_full(K, c->temporal_bias, c->color_fp16, w, u, j->t, src, flush, &j->W[p],
+                          &j->P[p], &j->key[p * K], &j->idx[p * K], &j->wt[p * K],
+                          &j->rgb[p * K * 3]);
+  }
+  return NULL;
+}
+
+int orc_push_frame_reproject(const orc_config* cfg, uint32_t t, const float* frame, int64_t pitch,
+                             float gx, float gy, const float* motion, const float* depth,
+                             const float* prev_depth, float depth_tol, const uint8_t* fov_map,
+                             const float* W0, const float* P0, const float* key0,
+                             const uint32_t* idx0, const float* wt0, const float* rgb0, float* W,
+                             float* P, float* key, uint32_t* idx, float* wt, float* rgb,
+                             int nthreads) {
+  if (!cfg || !frame || cfg->width <= 0 || cfg->height <= 0 || cfg->K < 1 || cfg->K > 16 ||
+      (cfg->rule != 0 && cfg->rule != 1) || (cfg->rule == 1 && cfg->K != 1) ||
+      cfg->temporal_bias < 0 || cfg->temporal_bias > 2 ||
+      pitch < 3 * (int64_t)cfg->width || !(cfg->r_f > 0.0f) || !isfinite(gx) || !isfinite(gy))
+    return -1;
+  if ((depth == NULL) != (prev_depth == NULL)) return -1;
+  if (depth && (!isfinite(depth_tol) || depth_tol < 0.0f)) return -1;
+  const int64_t hw = (int64_t)cfg->width * cfg->height;
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 256) nthreads = 256;
+  if ((int64_t)nthreads > hw) nthreads = (int)hw;
+  orc_rpjob jobs[256];
+  pthread_t th[256];
+  for (int k = 0; k < nthreads; ++k) {
+    memset(&jobs[k], 0, sizeof jobs[k]);
+    orc_job* j = &jobs[k].base;
+    j->cfg = cfg; j->t = t; j->frame = frame; j->pitch = pitch; j->gx = gx; j->gy = gy;
+    j->fov_map = fov_map; j->W = W; j->P = P; j->key = key; j->idx = idx; j->wt = wt;
+    j->rgb = rgb;
+    j->i0 = hw * k / nthreads;
+    j->i1 = hw * (k + 1) / nthreads;
+    jobs[k].motion = motion; jobs[k].depth = depth; jobs[k].prev_depth = prev_depth;
+    jobs[k].tol = depth_tol;
+    jobs[k].W0 = W0; jobs[k].P0 = P0; jobs[k].key0 = key0; jobs[k].idx0 = idx0;
+    jobs[k].wt0 = wt0; jobs[k].rgb0 = rgb0;
+  }
+  if (nthreads == 1) {
+    reproject_thread(&jobs[0]);
+    return 0;
+  }
+  for (int k = 0; k < nthreads; ++k) pthread_create(&th[k], NULL, reproject_thread, &jobs[k]);
+  for (int k = 0; k < nthreads; ++k) pthread_join(th[k], NULL);
+  return 0;
+}
+
 /* ---------------------------------------------------------------- statistics */
 
 void orc_run_streams(int K, int bias, int64_t n_trials, int n_items, const float* w,

@@ -115,6 +115,25 @@ int orc_push_frame(const orc_config* cfg, uint32_t t, const float* frame, int64_
                    float* wt, float* rgb, int nthreads);
 void orc_resolve(int K, int64_t npix, const uint32_t* idx, const float* wt, const float* rgb,
                  double* out, int nthreads);
+/* One frame with temporal reprojection (Sec. 4.3): pixel p = (x, y) takes as
+ * its history the previous frame's reservoir at q = (floor(x + 0.5 - mx),
+ * floor(y + 0.5 - my)), (mx, my) = motion[p] the screen motion in pixels since
+ * the previous frame (FP32 sub/add); the history is flushed when that centre
+ * lies outside the frame or, with depth buffers, when
+ * |prev_depth[q] - depth[p]| > depth_tol * depth[p] (FP32), as well as where
+ * fov_map is 0xFF. The new candidate is then combined as in orc_push_frame.
+ * Reads the previous state (all pixels, pixel-major) and writes the next one;
+ * the two must not overlap. motion [h][w][2] or NULL (no motion); depth and
+ * prev_depth [h][w] both or neither. Pinned: zero motion equals
+ * orc_push_frame, slot provenance under integer pans (closed form), flushes
+ * at depth edges and screen edges, nearest-centre rounding. Returns 0 or -1. */
+int orc_push_frame_reproject(const orc_config* cfg, uint32_t t, const float* frame, int64_t pitch,
+                             float gx, float gy, const float* motion, const float* depth,
+                             const float* prev_depth, float depth_tol, const uint8_t* fov_map,
+                             const float* W0, const float* P0, const float* key0,
+                             const uint32_t* idx0, const float* wt0, const float* rgb0, float* W,
+                             float* P, float* key, uint32_t* idx, float* wt, float* rgb,
+                             int nthreads);
 
 /* Statistics harness: n_trials independent single-pixel streams of n_items
  * candidates with weights w[n_items] and uniforms u[n_trials][n_items].

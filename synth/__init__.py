@@ -20,6 +20,7 @@ from .configs import WORKLOADS, Workload, StreamSpec, workload
 from .images import bilinear_level, block_counts, block_means, block_sums, box_pyramid, ground_truth
 from .foveate import Foveator, frame_pixels
 from .gaze import gaze_path
+from .scene import PanScene
 
 __all__ = ["WORKLOADS", "Workload", "StreamSpec", "workload", "ground_truth",
-           "box_pyramid", "block_means", "block_sums", "block_counts", "bilinear_level", "Foveator", "frame_pixels", "gaze_path"]
+           "box_pyramid", "block_means", "block_sums", "block_counts", "bilinear_level", "Foveator", "frame_pixels", "gaze_path", "PanScene"]

@@ -25,6 +25,7 @@ class StreamSpec:
     color_fp16: bool = False
     temporal_bias: bool = True
     update_rule: int = 0   # 0: key race over K slots, 1: literal n = 1 rule (K = 1)
+    pan_velocity: tuple | None = None   # camera pan in background pixels per frame (PanScene)
 
     @property
     def r_f(self) -> float:
@@ -66,6 +67,12 @@ def _mix_streams(frames: int, count: int = 16):
 
 
 WORKLOADS = {
+    "4k_pan": Workload(
+        "4k_pan", "3840x2160 RGB FP32, 240 frames, K=8, rings as 4k, a camera panning 3.25 px/frame "
+        "right and 0.75 px/frame down over a far grating background (depth 10) and 8 disks at depths "
+        "U[2,6] (parallax up to 16 px/frame); per-pixel motion vectors and depth; temporal "
+        "reprojection with a 5% relative depth test",
+        (StreamSpec(3840, 2160, 8, _RINGS_4K, seed=0, frames=240, pan_velocity=(3.25, 0.75)),)),
     "tiny": Workload(
         "tiny", "256x256 RGB FP32, 8 frames, K=4, fovea 32 px, 2x to 80 px, 4x beyond, "
         "gaze = centre + N(0, 4^2) px, Philox seed 0",

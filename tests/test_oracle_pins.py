@@ -704,3 +704,125 @@ def test_foveation_matches_the_input_generator():
         a, ra = oracle.foveate(fv.gt_numpy, radii, 20.3, 11.7, f)
         b, rb = fv.frame(20.3, 11.7)
         assert np.array_equal(ra, rb.numpy()) and np.array_equal(a, b.numpy())
+
+
+# ---------------------------------------------------------------- reprojection (Sec. 4.3)
+
+def _rp_frames(w, h, n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.random((n, h, w, 3)).astype(np.float32), rng.uniform(0, [w, h], size=(n, 2))
+
+
+@pytest.mark.parametrize("K,rule,bias", [(4, 0, 1), (3, 0, 2), (1, 1, 1), (2, 0, 0)])
+def test_reproject_without_motion_is_the_plain_push(K, rule, bias):
+    # zero motion and matching depth: every pixel keeps its own history, so
+    # the reprojected push reduces to the plain one bit for bit
+    w, h = 13, 9
+    frames, gaze = _rp_frames(w, h, 7, seed=K)
+    depth = np.full((h, w), 3.0, np.float32)
+    a = oracle.OracleStream(w, h, K, 3.0, seed=5, temporal_bias=bias, rule=rule)
+    b = oracle.OracleStream(w, h, K, 3.0, seed=5, temporal_bias=bias, rule=rule)
+    for t in range(7):
+        fm = None
+        if t == 4:
+            fm = np.zeros((h, w), np.uint8)
+            fm[2:5, 3:9] = 0xFF
+        a.push_frame(frames[t], gaze[t], fm)
+        mv = np.zeros((h, w, 2), np.float32) if t % 2 else None
+        b.push_frame_reproject(frames[t], gaze[t], mv, depth, depth, 0.01, fm)
+    sa, sb = a.state(), b.state()
+    for k in sa:
+        assert np.array_equal(sa[k].view(np.uint32) if sa[k].dtype == np.float32 else sa[k],
+                              sb[k].view(np.uint32) if sb[k].dtype == np.float32 else sb[k]), k
+
+
+@pytest.mark.parametrize("motion", [(2.0, -1.0), (2.3, -0.8), (1.7, -1.49)])
+def test_reproject_pan_slot_provenance(motion):
+    # with K above the frame count every candidate is inserted, so each slot's
+    # provenance follows in closed form: at a pan of s pixels per frame the
+    # history of p is the previous reservoir at p - s (nearest centre), and a
+    # chain that starts outside the frame restarts empty
+    w, h, K, T = 11, 8, 16, 6
+    frames, gaze = _rp_frames(w, h, T, seed=3)
+    st = oracle.OracleStream(w, h, K, 2.5, seed=9)
+    mv = np.broadcast_to(np.array(motion, np.float32), (h, w, 2)).copy()
+    sx, sy = int(np.floor(0.5 + motion[0])), int(np.floor(0.5 + motion[1]))  # integer source shift
+    prov = {(x, y): [(0, x, y)] for x in range(w) for y in range(h)}
+    st.push_frame_reproject(frames[0], gaze[0], mv)
+    for t in range(1, T):
+        st.push_frame_reproject(frames[t], gaze[t], mv)
+        nxt = {}
+        for x in range(w):
+            for y in range(h):
+                src = (x - sx, y - sy)
+                hist = prov[src] if (0 <= src[0] < w and 0 <= src[1] < h) else []
+                nxt[(x, y)] = hist + [(t, x, y)]
+        prov = nxt
+    s = st.state()
+    for (x, y), lst in prov.items():
+        p = y * w + x
+        occ = [j for j in range(K) if s["idx"][p, j] != oracle.EMPTY]
+        assert occ == list(range(len(lst))), (x, y)
+        for j, (f, xs, ys) in enumerate(lst):
+            assert s["idx"][p, j] == f
+            assert np.array_equal(s["rgb"][p, j], frames[f][ys, xs])
+            cfg = oracle.make_config(w, h, K, 2.5, seed=9)
+            assert s["wt"][p, j] == np.float32(oracle.weight32(cfg, xs, ys, *gaze[f]))
+
+
+def test_reproject_centre_rounding():
+    # the source is the pixel containing the moved centre: a motion of +0.5
+    # lands on the pixel's own left edge (kept), -0.5 on the right neighbour's
+    # left edge; 2^-10 past either edge crosses it (dyadic: every step exact)
+    w, h = 6, 3
+    frames, gaze = _rp_frames(w, h, 2, seed=1)
+    e = 2.0 ** -10
+    for m, shift in ((0.5, 0), (-0.5, 1), (0.5 + e, -1), (0.5 - e, 0), (-0.5 - e, 1),
+                     (-0.5 + e, 0)):
+        st = oracle.OracleStream(w, h, 4, 2.0, seed=2)
+        st.push_frame(frames[0], gaze[0])
+        mv = np.zeros((h, w, 2), np.float32)
+        mv[:, :, 0] = m
+        st.push_frame_reproject(frames[1], gaze[1], mv)
+        s = st.state()
+        for x in range(w):
+            src = x + shift
+            n_occ = int(np.sum(s["idx"][x] != oracle.EMPTY))
+            if 0 <= src < w:
+                assert n_occ == 2 and np.array_equal(s["rgb"][x, 0], frames[0][0, src])
+            else:
+                assert n_occ == 1
+    # vertically: -0.5 moves the bottom row's centres onto the frame's lower
+    # edge, which lies outside (the frame is [0, h) x [0, w))
+    st = oracle.OracleStream(w, h, 4, 2.0, seed=2)
+    st.push_frame(frames[0], gaze[0])
+    mv = np.zeros((h, w, 2), np.float32)
+    mv[:, :, 1] = -0.5
+    st.push_frame_reproject(frames[1], gaze[1], mv)
+    occ = np.sum(st.state()["idx"] != oracle.EMPTY, axis=1).reshape(h, w)
+    assert np.all(occ[:h - 1] == 2) and np.all(occ[h - 1] == 1)
+
+
+def test_reproject_depth_test_flushes_occlusions():
+    w, h = 8, 4
+    frames, gaze = _rp_frames(w, h, 3, seed=4)
+    cur = np.full((h, w), 4.0, np.float32)
+    prev = cur.copy()
+    prev[:, 2] = 5.0      # |5 - 4| = 1 = tol * 4: kept (strict test)
+    prev[:, 3] = 5.5      # beyond the tolerance: flushed
+    prev[:, 4] = 2.0      # a nearer surface moved away (disocclusion): flushed
+    st = oracle.OracleStream(w, h, 4, 2.0, seed=2)
+    st.push_frame(frames[0], gaze[0])
+    st.push_frame(frames[1], gaze[1])
+    st.push_frame_reproject(frames[2], gaze[2], None, cur, prev, 0.25)
+    s = st.state()
+    cfg = oracle.make_config(w, h, 4, 2.0, seed=2)
+    for x in range(w):
+        n_occ = int(np.sum(s["idx"][x] != oracle.EMPTY))
+        if x in (3, 4):
+            assert n_occ == 1 and s["idx"][x, 0] == 2
+            assert s["W"][x] == np.float32(oracle.weight32(cfg, x, 0, *gaze[2]))
+        else:
+            assert n_occ == 3
+    with pytest.raises(ValueError):
+        st.push_frame_reproject(frames[2], gaze[2], None, cur, None, 0.25)

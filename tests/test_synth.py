@@ -125,3 +125,32 @@ def test_block_means_order_and_bilinear():
     fv = Foveator(37, 21, (4.0, 9.0), seed=3, filter="bilinear")
     fr, lev = fv.frame(10.0, 10.0)
     assert fr.shape == (21, 37, 3) and np.all(fr.numpy() >= 0) and np.all(fr.numpy() <= 1)
+
+
+def test_pan_scene_motion_and_depth_are_consistent():
+    from synth import PanScene
+    sc = PanScene(96, 64, seed=3, velocity=(3.0, 1.0))
+    f0, m0, d0 = sc.render(4)
+    f1, m1, d1 = sc.render(5)
+    f0, f1, m1, d0, d1 = (a.numpy() for a in (f0, f1, m1, d0, d1))
+    assert f1.dtype == np.float32 and m1.shape == (64, 96, 2) and d1.shape == (64, 96)
+    assert f1.min() >= 0 and f1.max() <= 1
+    assert set(np.unique(d1)) <= set([10.0] + [np.float32(z) for z in sc.disk_z])
+    # the background moves by exactly -velocity per frame: where it is seen in
+    # both frames, a pixel shows what its motion vector points at
+    bg = np.argwhere(d1 == 10.0)
+    checked = 0
+    for y, x in bg[::7]:
+        py, px = int(y - m1[y, x, 1]), int(x - m1[y, x, 0])
+        if 0 <= py < 64 and 0 <= px < 96 and d0[py, px] == 10.0:
+            assert np.array_equal(f1[y, x], f0[py, px])
+            checked += 1
+    assert checked > 50
+    # nearer disks move faster (parallax)
+    assert np.abs(m1[d1 < 10.0]).max() > 3.0
+    assert np.array_equal(sc.render(5)[0].numpy(), f1)  # deterministic
+
+
+def test_pan_workload():
+    s = workload("4k_pan").streams[0]
+    assert s.pan_velocity == (3.25, 0.75) and s.pixels == 8294400
