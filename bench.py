@@ -422,6 +422,105 @@ def run_foveation(args, dev, spec, seed, gaze):
     return out
 
 
+def reproject_bytes_per_px(K: int, fp16: bool, literal: bool = False, fov: bool = True) -> int:
+    """Algorithmic bytes of one reprojected pixel-update: the gathered history
+    is read and every slot written to the other buffer, plus the frame,
+    motion vector, both depths, ring map and resolved output."""
+    slot = (4 + 4 + (4 + 6 + 2) if fp16 else 4 + 4 + 16) if not literal else (4 + (4 + 6 + 2 if fp16 else 16))
+    sums = 8 if not literal else 4   # W, P (W only for the literal rule)
+    return 2 * (sums + K * slot) + 12 + 8 + 8 + (1 if fov else 0) + 12
+
+
+def run_reprojection(args, dev):
+    """The 4K panning workload: temporal reprojection on every frame. Frames,
+    motion and depth of the 2.5-D scene are rendered on the device beforehand
+    (input generation) and foveated by the library's kernels; the timed loop
+    is one wrs_push_frame_reproject per frame (fused resolve, ring map, depth
+    test), and the full per-frame loop mip build -> foveate -> reprojected push
+    is timed separately."""
+    import paper_2510_03964_gb300 as wrs
+    from synth import PanScene
+    spec = workload("4k_pan").streams[0]
+    scene = PanScene(spec.width, spec.height, seed=spec.seed, velocity=spec.pan_velocity, device=dev)
+    gaze = gaze_path(spec.width, spec.height, spec.frames, seed=spec.seed)
+    nfr = args.reproj_frames
+    hw = spec.width * spec.height
+    stream = torch.cuda.Stream(device=dev)
+    levels = len(spec.radii) + 1
+    imgs, mvs, deps, frames, rings = [], [], [], [], []
+    with torch.cuda.stream(stream):
+        for t in range(nfr):
+            img, mv, dp = scene.render(t)
+            fov = wrs.Foveation(img, spec.radii, filter="bilinear", stream=stream)
+            fr, rg = fov.frame(gaze[t], stream=stream)
+            imgs.append(img); mvs.append(mv); deps.append(dp); frames.append(fr); rings.append(rg)
+    torch.cuda.synchronize()
+    out = torch.empty_like(frames[0])
+    st = wrs.Stream(spec.width, spec.height, spec.K, spec.r_f, seed=spec.seed, device=dev, stream=stream)
+    st.set_reprojection_buffer(stream=stream)
+    tol = 0.05
+
+    def push(t):
+        i = t % nfr
+        st.push_frame_reproject(frames[i], gaze[i], mvs[i], deps[i], deps[i - 1], tol, rings[i], out,
+                                stream=stream)
+
+    with torch.cuda.stream(stream):
+        st.push_frame(frames[0], gaze[0], rings[0], out, stream=stream)
+        for t in range(1, 1 + args.warmup):
+            push(t)
+        torch.cuda.synchronize()
+        r0 = st.replacements(stream=stream)
+        steps = args.reproj_steps
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            ev[k][0].record(stream)
+            push(1 + args.warmup + k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        rho = (st.replacements(stream=stream) - r0) / float(hw * steps)
+        times = [a.elapsed_time(b) for a, b in ev]
+        total = ev[0][0].elapsed_time(ev[-1][1])
+
+        # the per-frame loop with the post-process on the device too
+        mip = wrs.mip_build(imgs[0], levels, stream=stream)
+        fr = torch.empty_like(frames[0])
+        rg = torch.empty_like(rings[0])
+
+        def full(t):
+            i = t % nfr
+            wrs.mip_build(imgs[i], levels, out=mip, stream=stream)
+            wrs.foveate(imgs[i], mip, spec.radii, gaze[i], "bilinear", out=fr, ring_map=rg, stream=stream)
+            st.push_frame_reproject(fr, gaze[i], mvs[i], deps[i], deps[i - 1], tol, rg, out, stream=stream)
+
+        for t in range(3):
+            full(t + 1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for t in range(args.reproj_steps):
+            full(t + 4)
+        b.record(stream)
+        torch.cuda.synchronize()
+    st.close()
+    peaks = measured_peaks()
+    bpp = reproject_bytes_per_px(spec.K, False)
+    ms = statistics.median(times)
+    gbs = bpp * hw / (ms * 1e-3) / 1e9
+    return {"workload": workload("4k_pan").description,
+            "ms_per_frame": round(total / steps, 4), "kernel_ms_median": round(ms, 4), "steps": steps,
+            "frames_distinct": nfr, "replacement_rate": round(rho, 4),
+            "mpx_updates_per_s": round(hw / (ms * 1e-3) / 1e6, 1),
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": round(gbs / peaks["hbm_gbs"], 4), "algorithmic_bytes_per_px": bpp,
+                         "bytes_rule": "history read (W, P, K slots of key, idx, record) + every slot "
+                                       "written to the other buffer + frame 12 + motion 8 + depths 8 + "
+                                       "ring map 1 + output 12",
+                         "kernel": "reproject_kernel<fp32>"},
+            "loop_mip_foveate_reproject_ms_per_frame": round(a.elapsed_time(b) / args.reproj_steps, 4),
+            "note": "the frames' images, motion and depth are rendered on the device before the "
+                    "timed region; inputs (1.9 GB of state per buffer) exceed L2"}
+
+
 def run_serving(args, dev):
     """The 64-viewer serving trace at the workload's frame rates (72-120 Hz per
     viewer) and at an overload (200-300 Hz), batched vs one launch per frame."""
@@ -542,6 +641,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.empty_cache()
     foveation = run_foveation(args, dev, spec, seed, gaze) if args.fov_reps > 0 else None
     torch.cuda.empty_cache()
+    reprojection = run_reprojection(args, dev) if args.reproj_steps > 0 else None
+    torch.cuda.empty_cache()
     serving = run_serving(args, dev) if args.serve > 0 else None
     torch.cuda.empty_cache()
 
@@ -584,6 +685,7 @@ def run_ours(args, world, rank, local):
         "e2e": e2e,
         "batched": batched,
         "foveation": foveation,
+        "reprojection": reprojection,
         "serving": serving,
     }
     if args.cpu_baseline:
@@ -625,6 +727,10 @@ def main():
     ap.add_argument("--fov-reps", type=int, default=50,
                     help="timed calls of each foveation kernel (0 skips the foveation section)")
     ap.add_argument("--fov-loop-frames", type=int, default=200)
+    ap.add_argument("--reproj-steps", type=int, default=200,
+                    help="timed reprojected pushes on the 4K pan (0 skips the section)")
+    ap.add_argument("--reproj-frames", type=int, default=32,
+                    help="distinct rendered frames of the pan, cycled")
     ap.add_argument("--serve", type=float, default=8.0,
                     help="seconds of the 64-viewer serving trace per mode and load (0 skips it)")
     args = ap.parse_args()

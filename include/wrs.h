@@ -239,6 +239,46 @@ int wrs_push_batch(wrs_batch* batch, int n, wrs_ctx* const* ctxs, const float* c
 int wrs_get_stats(wrs_ctx* ctx, uint64_t* replacements, wrs_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Temporal reprojection (Sec. 4.3, "Implementation"): after camera or scene
+ * motion each pixel continues the reservoir of the surface it now shows,
+ * found through a motion vector, and a depth comparison between frames drops
+ * that history where the surface was occluded or disoccluded.
+ * ------------------------------------------------------------------------ */
+
+/* Gives the stream a second state buffer (d_spare, wrs_state_bytes bytes,
+ * 256-byte aligned, caller-owned, on the stream's device): a reprojected push
+ * reads the previous reservoirs from one buffer and writes the new ones to
+ * the other, and the two swap roles after every reprojected push. Plain
+ * pushes, resolves, exports and imports always act on whichever buffer holds
+ * the current reservoirs; the status word and counters stay in the header of
+ * the buffer given to wrs_create. d_spare = NULL detaches the spare buffer,
+ * first copying the current reservoirs back into the primary buffer if they
+ * live in the spare (enqueued on `stream`). Errors: WRS_ERR_ARG, WRS_ERR_BUDGET
+ * (buffer too small), WRS_ERR_CUDA. */
+int wrs_set_reprojection_buffer(wrs_ctx* ctx, void* d_spare, size_t bytes, wrs_stream_t stream);
+
+/* One frame with temporal reprojection. Pixel p = (x, y) continues the
+ * previous frame's reservoir at the pixel q containing the point
+ * (x + 0.5 - mx, y + 0.5 - my), (mx, my) = d_motion[p] the screen-space motion
+ * in pixels of the surface seen at p since the previous frame (FP32 sub/add;
+ * NULL = no motion). The history is flushed (reservoir emptied, as a 0xFF fov
+ * map entry does) when that point lies outside [0, width) x [0, height), when
+ * depth buffers are given and |d_prev_depth[q] - d_depth[p]| >
+ * depth_tol * d_depth[p] (FP32; view depths of the surfaces at p now and at q
+ * in the previous frame), or where d_fov_map is 0xFF. Then the frame's
+ * candidate is combined exactly as wrs_push_frame does (same weight, uniform
+ * and key race), every slot is written to the other state buffer and the
+ * buffers swap. d_motion: [height][width] float pairs (8-byte aligned);
+ * d_depth, d_prev_depth: [height][width] floats, both or neither; the rest as
+ * for wrs_push_frame. Requires wrs_set_reprojection_buffer. Errors: as
+ * wrs_push_frame, plus WRS_ERR_STATE without a spare buffer and WRS_ERR_ARG for
+ * a bad depth_tol (negative or not finite) or a lone depth buffer. */
+int wrs_push_frame_reproject(wrs_ctx* ctx, const float* d_frame, int64_t frame_pitch_elems,
+                             float gaze_x, float gaze_y, const float* d_motion,
+                             const float* d_depth, const float* d_prev_depth, float depth_tol,
+                             const uint8_t* d_fov_map, float* d_out, wrs_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Foveation post-process (Sec. 4.3, "Implementation"): the paper simulates
  * foveated rendering on the rendered frame by mip-mapping it and
  * reconstructing each ring around the gaze from a coarser level with

@@ -65,6 +65,9 @@ SIGNATURES = {
     "wrs_batch_get_launch": (_I, [_V, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "wrs_push_batch": (_I, [_V, _I, _V, _V, _V, _V, _V, _V]),
     "wrs_get_stats": (_I, [_V, C.POINTER(C.c_uint64), _V]),
+    "wrs_set_reprojection_buffer": (_I, [_V, _V, C.c_size_t, _V]),
+    "wrs_push_frame_reproject": (_I, [_V, _V, C.c_int64, C.c_float, C.c_float, _V, _V, _V, C.c_float,
+                                      _V, _V, _V]),
     "wrs_mip_layout_get": (_I, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(WrsMipLayout)]),
     "wrs_mip_build": (_I, [_V, C.c_int64, C.c_int32, C.c_int32, C.c_int32, _V, C.c_size_t, _V]),
     "wrs_foveate": (_I, [_V, C.c_int64, _V, C.c_size_t, C.c_int32, C.c_int32, C.c_int32, _V,

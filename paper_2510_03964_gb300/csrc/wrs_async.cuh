@@ -176,6 +176,7 @@ __device__ __forceinline__ int compute_tile(const StreamDev& s, const FrameDev& 
   src.W = reinterpret_cast<const float*>(st + L.W);
   src.P = reinterpret_cast<const float*>(st + L.P);
   src.key = reinterpret_cast<const float*>(st + L.key);
+  src.idx = nullptr;
   src.wt = reinterpret_cast<const float*>(st + L.wt);
   src.col = st + L.col;
   src.stride = T;

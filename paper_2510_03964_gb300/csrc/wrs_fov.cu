@@ -281,6 +281,7 @@ int device_sms(int* sms) {
 
 extern "C" int wrs_mip_layout_get(int32_t width, int32_t height, int32_t levels,
                                   wrs_mip_layout* out) {
+  wrs_clear_error();
   if (!out) return wrs_fail(WRS_ERR_ARG, "layout output is NULL");
   if (int rc = check_image(width, height)) return rc;
   if (levels < 1 || levels > WRS_MAX_MIP_LEVELS)
@@ -303,6 +304,7 @@ extern "C" int wrs_mip_layout_get(int32_t width, int32_t height, int32_t levels,
 
 extern "C" int wrs_mip_build(const float* d_img, int64_t pitch, int32_t width, int32_t height,
                              int32_t levels, void* d_mip, size_t mip_bytes, wrs_stream_t stream) {
+  wrs_clear_error();
   wrs_mip_layout L;
   if (int rc = wrs_mip_layout_get(width, height, levels, &L)) return rc;
   if (levels == 1) return WRS_OK;
@@ -346,6 +348,7 @@ extern "C" int wrs_foveate(const float* d_img, int64_t pitch, const void* d_mip,
                            int32_t width, int32_t height, int32_t nradii, const float* radii,
                            float gx, float gy, int32_t filter, float* d_frame,
                            int64_t frame_pitch, uint8_t* d_ring, wrs_stream_t stream) {
+  wrs_clear_error();
   if (int rc = check_image(width, height)) return rc;
   if (nradii < 1 || nradii > WRS_MAX_MIP_LEVELS - 1 || !radii)
     return wrs_fail(WRS_ERR_ARG, "nradii must be in 1..%d with a radii array",

@@ -9,7 +9,9 @@
 struct wrs_ctx {
   wrs_config cfg;
   wrs_layout lay;
-  uint8_t* state;        // caller-owned device buffer
+  uint8_t* state;        // caller-owned device buffer: header (status, counters) + planes
+  uint8_t* planes;       // buffer whose planes hold the current reservoirs: state or spare
+  uint8_t* spare;        // caller-owned second buffer for reprojection (null until set)
   uint32_t t;            // frames pushed
   int block;             // threads per block of the plain kernel
   int px;                // requested pixels per thread of the plain kernel
@@ -36,12 +38,14 @@ cudaError_t wrs_launch_pipe(const wrs::StreamDev& s, const wrs::FrameDev& f, boo
                             uint64_t timeout_ns, uint32_t extra_tx, cudaStream_t st);
 void wrs_default_pipe(int K, bool f16, int* px, int* stages);
 
+void wrs_clear_error();
 int wrs_fail(int code, const char* fmt, ...);
 int wrs_cuda_fail(cudaError_t e, const char* what);
 int wrs_check_config(const wrs_config* c);
 void wrs_make_layout(const wrs_config* c, wrs_layout* L);
 float wrs_delta(const wrs_config* c);
 wrs::StreamDev wrs_stream_dev(const wrs_ctx* x);
+cudaError_t wrs_init_planes(const wrs_ctx* x, uint8_t* base, cudaStream_t st);
 int wrs_effective_px(const wrs_ctx* x, const float* frame, int64_t pitch, const float* out);
 cudaError_t wrs_launch_push(const wrs::StreamDev& s, const wrs::FrameDev& f, int block, int px,
                             bool f16, cudaStream_t st);

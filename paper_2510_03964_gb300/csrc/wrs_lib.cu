@@ -31,7 +31,7 @@ int wrs_fail(int code, const char* fmt, ...) {
   return code;
 }
 
-static void clear_error() { g_err[0] = '\0'; }
+void wrs_clear_error() { g_err[0] = '\0'; }
 
 extern "C" const char* wrs_last_error(void) { return g_err; }
 
@@ -99,7 +99,7 @@ float wrs_delta(const wrs_config* c) {
 
 StreamDev wrs_stream_dev(const wrs_ctx* x) {
   StreamDev s;
-  uint8_t* b = x->state;
+  uint8_t* b = x->planes;
   s.W = reinterpret_cast<float*>(b + x->lay.W_off);
   s.P = reinterpret_cast<float*>(b + x->lay.P_off);
   s.key = reinterpret_cast<float*>(b + x->lay.key_off);
@@ -298,9 +298,23 @@ cudaError_t wrs_launch_push(const StreamDev& s, const FrameDev& f, int block, in
 
 // ---------------------------------------------------------------- C-ABI
 
+cudaError_t wrs_init_planes(const wrs_ctx* x, uint8_t* base, cudaStream_t st) {
+  // colour planes zeroed, then empty slots, W = 0, P = 1 in the planes at `base`
+  wrs_ctx tmp = *x;
+  tmp.planes = base;
+  const StreamDev s = wrs_stream_dev(&tmp);
+  zero_kernel<<<1216, 256, 0, st>>>(base + x->lay.col_off, x->lay.total_bytes - x->lay.col_off);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    init_kernel<<<1216, 256, 0, st>>>(s);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
 extern "C" int wrs_create(const wrs_config* cfg, void* d_state, size_t state_bytes,
                           wrs_stream_t stream, wrs_ctx** out) {
-  clear_error();
+  wrs_clear_error();
   if (!out) return wrs_fail(WRS_ERR_ARG, "output context pointer is NULL");
   *out = nullptr;
   int rc = wrs_check_config(cfg);
@@ -317,6 +331,8 @@ extern "C" int wrs_create(const wrs_config* cfg, void* d_state, size_t state_byt
   x->cfg = *cfg;
   x->lay = L;
   x->state = static_cast<uint8_t*>(d_state);
+  x->planes = x->state;
+  x->spare = nullptr;
   x->t = 0;
   x->block = kDefaultBlock;
   x->px = kDefaultPx;
@@ -333,19 +349,10 @@ extern "C" int wrs_create(const wrs_config* cfg, void* d_state, size_t state_byt
     return wrs_cuda_fail(e, "wrs_create: device query");
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const StreamDev s = wrs_stream_dev(x);
   // status word and colour planes start zeroed; then the per-slot fields
   zero_kernel<<<1, 32, 0, st>>>(x->state + L.status_off, kStatusBytes);
   e = cudaGetLastError();
-  const int64_t col_bytes = L.total_bytes - L.col_off;
-  if (e == cudaSuccess) {
-    zero_kernel<<<1216, 256, 0, st>>>(x->state + L.col_off, col_bytes);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) {
-    init_kernel<<<1216, 256, 0, st>>>(s);
-    e = cudaGetLastError();
-  }
+  if (e == cudaSuccess) e = wrs_init_planes(x, x->state, st);
   if (e != cudaSuccess) {
     delete x;
     return wrs_cuda_fail(e, "wrs_create: init launch");
@@ -357,7 +364,7 @@ extern "C" int wrs_create(const wrs_config* cfg, void* d_state, size_t state_byt
 extern "C" int wrs_push_frame(wrs_ctx* x, const float* d_frame, int64_t pitch, float gx,
                               float gy, const uint8_t* d_fov, float* d_out,
                               wrs_stream_t stream) {
-  clear_error();
+  wrs_clear_error();
   if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
   if (!d_frame) return wrs_fail(WRS_ERR_ARG, "d_frame is NULL");
   if (!aligned(d_frame, 4) || (d_out && !aligned(d_out, 4)))
@@ -393,7 +400,7 @@ extern "C" int wrs_push_frame(wrs_ctx* x, const float* d_frame, int64_t pitch, f
 }
 
 extern "C" int wrs_resolve(wrs_ctx* x, float* d_out, wrs_stream_t stream) {
-  clear_error();
+  wrs_clear_error();
   if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
   if (!d_out || !aligned(d_out, 4)) return wrs_fail(WRS_ERR_ARG, "d_out is NULL or unaligned");
   const StreamDev s = wrs_stream_dev(x);
@@ -406,7 +413,7 @@ extern "C" int wrs_resolve(wrs_ctx* x, float* d_out, wrs_stream_t stream) {
 }
 
 extern "C" int wrs_destroy(wrs_ctx* x) {
-  clear_error();
+  wrs_clear_error();
   delete x;
   return WRS_OK;
 }
@@ -415,7 +422,7 @@ extern "C" int wrs_push_frame_host(wrs_ctx* x, const float* h_frame, float gx, f
                                    const uint8_t* h_fov, float* h_out, float* d_frame_stage,
                                    uint8_t* d_fov_stage, float* d_out_stage,
                                    wrs_stream_t stream) {
-  clear_error();
+  wrs_clear_error();
   if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
   if (!h_frame || !h_out || !d_frame_stage || !d_out_stage)
     return wrs_fail(WRS_ERR_ARG, "frame, out and their staging buffers must be non-NULL");
@@ -437,13 +444,19 @@ extern "C" int wrs_push_frame_host(wrs_ctx* x, const float* h_frame, float gx, f
 }
 
 extern "C" int wrs_export_state(wrs_ctx* x, void* h_dst, size_t bytes, wrs_stream_t stream) {
-  clear_error();
+  wrs_clear_error();
   if (!x || !h_dst) return wrs_fail(WRS_ERR_ARG, "context or destination is NULL");
   if (bytes < static_cast<size_t>(x->lay.total_bytes))
     return wrs_fail(WRS_ERR_BUDGET, "destination holds %zu bytes, the state is %lld", bytes,
                     static_cast<long long>(x->lay.total_bytes));
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(h_dst, x->state, x->lay.total_bytes, cudaMemcpyDeviceToHost, st);
+  // the header from the primary buffer, the planes from whichever buffer holds them
+  const int64_t hdr = x->lay.W_off;
+  uint8_t* dst = static_cast<uint8_t*>(h_dst);
+  cudaError_t e = cudaMemcpyAsync(dst, x->state, hdr, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dst + hdr, x->planes + hdr, x->lay.total_bytes - hdr,
+                        cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_export_state");
   return WRS_OK;
@@ -451,13 +464,18 @@ extern "C" int wrs_export_state(wrs_ctx* x, void* h_dst, size_t bytes, wrs_strea
 
 extern "C" int wrs_import_state(wrs_ctx* x, const void* h_src, size_t bytes,
                                 uint32_t frame_index, wrs_stream_t stream) {
-  clear_error();
+  wrs_clear_error();
   if (!x || !h_src) return wrs_fail(WRS_ERR_ARG, "context or source is NULL");
   if (bytes < static_cast<size_t>(x->lay.total_bytes))
     return wrs_fail(WRS_ERR_BUDGET, "source holds %zu bytes, the state is %lld", bytes,
                     static_cast<long long>(x->lay.total_bytes));
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(x->state, h_src, x->lay.total_bytes, cudaMemcpyHostToDevice, st);
+  const int64_t hdr = x->lay.W_off;
+  const uint8_t* src = static_cast<const uint8_t*>(h_src);
+  cudaError_t e = cudaMemcpyAsync(x->state, src, hdr, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(x->planes + hdr, src + hdr, x->lay.total_bytes - hdr,
+                        cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_import_state");
   x->t = frame_index;
@@ -467,7 +485,7 @@ extern "C" int wrs_import_state(wrs_ctx* x, const void* h_src, size_t bytes,
 extern "C" uint32_t wrs_frame_index(const wrs_ctx* x) { return x ? x->t : 0u; }
 
 extern "C" int wrs_set_launch(wrs_ctx* x, int block_threads, int px_per_thread) {
-  clear_error();
+  wrs_clear_error();
   if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
   if (block_threads == 0) block_threads = kDefaultBlock;
   if (px_per_thread == 0) px_per_thread = kDefaultPx;
@@ -490,7 +508,7 @@ extern "C" int wrs_get_launch(const wrs_ctx* x, int* block_threads, int* px_per_
 
 extern "C" int wrs_set_pipeline(wrs_ctx* x, int enable, int px_per_thread, int stages,
                                 int ctas_per_sm) {
-  clear_error();
+  wrs_clear_error();
   if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
   int dpx, dst;
   wrs_default_pipe(x->cfg.K, x->cfg.color_fp16 != 0, &dpx, &dst);
@@ -528,7 +546,7 @@ extern "C" int wrs_get_pipeline(const wrs_ctx* x, int* enable, int* px_per_threa
 }
 
 extern "C" int wrs_set_wait_limit(wrs_ctx* x, uint64_t timeout_ns, uint32_t test_extra_tx) {
-  clear_error();
+  wrs_clear_error();
   if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
   if (timeout_ns == 0) timeout_ns = kDefaultTimeoutNs;
   if (timeout_ns > 60ull * 1000000000ull) return wrs_fail(WRS_ERR_ARG, "timeout above 60 s");
@@ -539,7 +557,7 @@ extern "C" int wrs_set_wait_limit(wrs_ctx* x, uint64_t timeout_ns, uint32_t test
 }
 
 extern "C" int wrs_check_status(wrs_ctx* x, wrs_stream_t stream) {
-  clear_error();
+  wrs_clear_error();
   if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint32_t word = 0;
@@ -557,7 +575,7 @@ extern "C" int wrs_check_status(wrs_ctx* x, wrs_stream_t stream) {
 }
 
 extern "C" int wrs_get_stats(wrs_ctx* x, uint64_t* replacements, wrs_stream_t stream) {
-  clear_error();
+  wrs_clear_error();
   if (!x || !replacements) return wrs_fail(WRS_ERR_ARG, "NULL argument");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   unsigned long long v = 0;

@@ -75,6 +75,7 @@ class Stream:
         elif state.numel() < self.nbytes:
             raise ValueError("state buffer too small")
         self.state = state
+        self.spare = None
         self.device = state.device
         ctx = C.c_void_p()
         with torch.cuda.device(self.device):
@@ -114,6 +115,44 @@ class Stream:
             pass
 
     # -- extras ----------------------------------------------------------------
+    def set_reprojection_buffer(self, spare: torch.Tensor | None = "alloc", stream=None):
+        """Attach a second state buffer (allocated when not given) so that
+        push_frame_reproject can gather from the previous frame's reservoirs;
+        None detaches it."""
+        if isinstance(spare, str):
+            spare = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        if spare is not None and spare.device != self.device:
+            raise ValueError("the spare buffer must be on the stream's device")
+        with torch.cuda.device(self.device):
+            check(load().wrs_set_reprojection_buffer(
+                self._ctx, None if spare is None else _dev_ptr(spare, torch.uint8, "spare"),
+                0 if spare is None else spare.numel(), _stream_handle(stream)))
+        self.spare = spare
+
+    def push_frame_reproject(self, frame: torch.Tensor, gaze, motion: torch.Tensor | None = None,
+                             depth: torch.Tensor | None = None, prev_depth: torch.Tensor | None = None,
+                             depth_tol: float = 0.05, fov_map: torch.Tensor | None = None,
+                             out: torch.Tensor | None = None, stream=None):
+        """One frame with temporal reprojection: motion [H][W][2] float32
+        (pixels moved since the previous frame), depth / prev_depth [H][W]
+        float32 (view depth now and in the previous frame)."""
+        if tuple(frame.shape) != (self.height, self.width, 3) or frame.stride(2) != 1 or frame.stride(1) != 3:
+            raise ValueError("frame must be a [H][W][3] float32 tensor with packed pixels")
+        for t, shape, name in ((motion, (self.height, self.width, 2), "motion"),
+                               (depth, (self.height, self.width), "depth"),
+                               (prev_depth, (self.height, self.width), "prev_depth"),
+                               (fov_map, (self.height, self.width), "fov_map"),
+                               (out, (self.height, self.width, 3), "out")):
+            if t is not None and (tuple(t.shape) != shape or not t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous tensor of shape {shape}")
+        with torch.cuda.device(self.device):
+            check(load().wrs_push_frame_reproject(
+                self._ctx, _dev_ptr(frame, torch.float32, "frame"), int(frame.stride(0)),
+                float(gaze[0]), float(gaze[1]), _dev_ptr(motion, torch.float32, "motion"),
+                _dev_ptr(depth, torch.float32, "depth"), _dev_ptr(prev_depth, torch.float32, "prev_depth"),
+                float(depth_tol), _dev_ptr(fov_map, torch.uint8, "fov_map"),
+                _dev_ptr(out, torch.float32, "out"), _stream_handle(stream)))
+
     @property
     def frame_index(self) -> int:
         return int(load().wrs_frame_index(self._ctx))
