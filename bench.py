@@ -440,7 +440,8 @@ def run_reprojection(args, dev):
     is timed separately."""
     import paper_2510_03964_gb300 as wrs
     from synth import PanScene
-    spec = workload("4k_pan").streams[0]
+    wl = workload(args.reproj_workload)
+    spec = wl.streams[0]
     scene = PanScene(spec.width, spec.height, seed=spec.seed, velocity=spec.pan_velocity, device=dev)
     gaze = gaze_path(spec.width, spec.height, spec.frames, seed=spec.seed)
     nfr = args.reproj_frames
@@ -506,7 +507,7 @@ def run_reprojection(args, dev):
     bpp = reproject_bytes_per_px(spec.K, False)
     ms = statistics.median(times)
     gbs = bpp * hw / (ms * 1e-3) / 1e9
-    return {"workload": workload("4k_pan").description,
+    return {"workload": wl.description,
             "ms_per_frame": round(total / steps, 4), "kernel_ms_median": round(ms, 4), "steps": steps,
             "frames_distinct": nfr, "replacement_rate": round(rho, 4),
             "mpx_updates_per_s": round(hw / (ms * 1e-3) / 1e6, 1),
@@ -537,7 +538,7 @@ def workload_config(spec, name):
     return {"workload": f"{name}: {spec.width}x{spec.height} RGB, K={spec.K}, "
                         f"{'FP16' if spec.color_fp16 else 'FP32'} colour planes, fovea {spec.r_f:g} px, "
                         f"rings {','.join(f'{r:g}' for r in spec.radii)} px, {spec.frames} distinct frames "
-                        f"pushed cyclically, temporal bias {'on' if spec.temporal_bias else 'off'}",
+                        f"pushed cyclically, temporal bias {['off', 'Eq. (temporal-bias)', 'Eq. (full-temporal-bias)'][int(spec.temporal_bias)]}",
             "width": spec.width, "height": spec.height, "K": spec.K,
             "color": "fp16" if spec.color_fp16 else "fp32", "frames_distinct": spec.frames,
             "l2": "state+frame traffic per step far above the 129 MB L2; no flush",
@@ -708,7 +709,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="4k",
-                    choices=["4k", "4k_fp16", "hd", "hd_k8", "tiny", "4k_k1", "4k_k1_literal"])
+                    choices=["4k", "4k_fp16", "hd", "hd_k8", "tiny", "4k_k1", "4k_k1_literal", "4k_bias2"])
     ap.add_argument("--distinct-frames", type=int, default=0,
                     help="frames resident in HBM (default: all of the workload's)")
     ap.add_argument("--pipe", type=int, default=1, help="1: pipelined kernel (default), 0: plain")
@@ -729,6 +730,7 @@ def main():
     ap.add_argument("--fov-loop-frames", type=int, default=200)
     ap.add_argument("--reproj-steps", type=int, default=200,
                     help="timed reprojected pushes on the 4K pan (0 skips the section)")
+    ap.add_argument("--reproj-workload", default="4k_pan", choices=["4k_pan", "hd_pan"])
     ap.add_argument("--reproj-frames", type=int, default=32,
                     help="distinct rendered frames of the pan, cycled")
     ap.add_argument("--serve", type=float, default=8.0,

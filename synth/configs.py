@@ -23,7 +23,7 @@ class StreamSpec:
     gaze_model: str = "saccades"
     jitter_px: float = 6.0
     color_fp16: bool = False
-    temporal_bias: bool = True
+    temporal_bias: int = 1     # 0 none, 1 Eq. (temporal-bias), 2 Eq. (full-temporal-bias)
     update_rule: int = 0   # 0: key race over K slots, 1: literal n = 1 rule (K = 1)
     pan_velocity: tuple | None = None   # camera pan in background pixels per frame (PanScene)
 
@@ -96,6 +96,13 @@ WORKLOADS = {
         "4k_k1_literal", "as 4k_k1 with the literal n = 1 rule (rand * (R1 + R2) <= R1 keeps R1 "
         "after the temporal bias; no keys, no bias product)",
         (StreamSpec(3840, 2160, 1, _RINGS_4K, seed=0, frames=240, update_rule=1),)),
+    "4k_bias2": Workload(
+        "4k_bias2", "as 4k with the full temporal bias (Eq. full-temporal-bias): the history's "
+        "weight also scales by 1 - |Delta L*|/100 against the new sample",
+        (StreamSpec(3840, 2160, 8, _RINGS_4K, seed=0, frames=240, temporal_bias=2),)),
+    "hd_pan": Workload(
+        "hd_pan", "as 4k_pan at 1920x1080 with the hd rings and K=8 (profiling case)",
+        (StreamSpec(1920, 1080, 8, _RINGS_HD, seed=0, frames=120, pan_velocity=(3.25, 0.75)),)),
     "4k_fp16": Workload(
         "4k_fp16", "as 4k with FP16 colour planes (keys, weights and accumulation FP32)",
         (StreamSpec(3840, 2160, 8, _RINGS_4K, seed=0, frames=240, color_fp16=True),)),
