@@ -317,13 +317,14 @@ def run_batched(args, dev):
 
 
 def _timed_flushed(fn, reps: int, stream, flush: torch.Tensor) -> list:
-    """Per-call device times (ms) with the L2 flushed (a write larger than L2)
-    before every call, outside the timed region."""
+    """Per-call device times (ms) with the L2 flushed before every call,
+    outside the timed region: a read of a buffer larger than L2 (a read leaves
+    no dirty lines whose write-back would land inside the timed call)."""
     times = []
     for _ in range(3):
         fn()
     for _ in range(reps):
-        flush.add_(1)
+        flush.sum()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         fn()
@@ -346,12 +347,12 @@ def run_foveation(args, dev, spec, seed, gaze):
     levels = len(spec.radii) + 1
     lay = wrs.mip_layout(spec.width, spec.height, levels)
     texels = [lay.width[L] * lay.height[L] for L in range(1, levels)]
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     reps = args.fov_reps
     peaks = measured_peaks()
     out = {"image": f"{spec.width}x{spec.height} RGB f32, {levels} levels, radii {list(spec.radii)}",
            "timing": f"median of {reps} calls, CUDA events on the launching stream, L2 flushed "
-                     f"(256 MB write) before each call"}
+                     f"(256 MB read) before each call"}
     with torch.cuda.stream(stream):
         mip = wrs.mip_build(img, levels, stream=stream)
         t_mip = _timed_flushed(lambda: wrs.mip_build(img, levels, out=mip, stream=stream), reps, stream, flush)
@@ -412,6 +413,25 @@ def run_foveation(args, dev, spec, seed, gaze):
         total = ev[0][0].elapsed_time(ev[-1][2])
         fov_ms = statistics.median(e[0].elapsed_time(e[1]) for e in ev)
         push_ms = statistics.median(e[1].elapsed_time(e[2]) for e in ev)
+        # the same loop with the frame foveated inside the update kernel
+        fovobj = wrs.Foveation(img, spec.radii, filter="bilinear", stream=stream)
+        st2 = wrs.Stream(spec.width, spec.height, spec.K, spec.r_f, seed=seed, stream_id=spec.stream_id,
+                         color_fp16=spec.color_fp16, temporal_bias=spec.temporal_bias, device=dev,
+                         stream=stream, update_rule=spec.update_rule)
+        for t in range(5):
+            st2.push_foveated(fovobj, gaze[t % len(gaze)], None, res, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in range(n_loop):
+            st2.push_foveated(fovobj, gaze[(5 + t) % len(gaze)], None, res, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        st2.close()
+        out["loop_push_foveated"] = {
+            "ms_per_frame": round(e0.elapsed_time(e1) / n_loop, 4), "frames": n_loop,
+            "note": "per frame: one wrs_push_foveated (bilinear): the update kernel foveates each "
+                    "pixel from the image and its mip levels as it reads the pixel's reservoir; "
+                    "fused resolve; no frame in memory"}
         out["loop_foveate_push_resolve"] = {
             "ms_per_frame": round(total / n_loop, 4), "frames": n_loop,
             "foveate_ms_median": round(fov_ms, 4), "push_ms_median": round(push_ms, 4),

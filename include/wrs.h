@@ -344,7 +344,21 @@ int wrs_foveate(const float* d_img, int64_t img_pitch_elems, const void* d_mip, 
                 float gaze_y, int32_t filter, float* d_frame, int64_t frame_pitch_elems,
                 uint8_t* d_ring_map, wrs_stream_t stream);
 
-/* Message of the last failed call on this thread ("" if none). */
+/* wrs_foveate followed by wrs_push_frame in one pass, without the frame in
+ * memory: the update kernel foveates each pixel of the frame (same ring test,
+ * texels and arithmetic as wrs_foveate, so the reservoirs and the output are
+ * bit-identical to the two calls) as it reads the pixel's reservoir. d_img,
+ * img_pitch_elems, d_mip, mip_bytes, nradii, radii and filter as for
+ * wrs_foveate (the image is width x height of the stream); gaze, d_fov_map
+ * (a flush map: only 0xFF matters) and d_out as for wrs_push_frame. Needs
+ * width % 4 == 0 and d_out 16-byte aligned; always takes the pipelined kernel
+ * with one pixel per thread. Errors: as wrs_foveate and wrs_push_frame. */
+int wrs_push_foveated(wrs_ctx* ctx, const float* d_img, int64_t img_pitch_elems,
+                      const void* d_mip, size_t mip_bytes, int32_t nradii, const float* radii,
+                      int32_t filter, float gaze_x, float gaze_y, const uint8_t* d_fov_map,
+                      float* d_out, wrs_stream_t stream);
+
+/* Message of the last failed call on this thread ("" if none). *//* Message of the last failed call on this thread ("" if none). */
 const char* wrs_last_error(void);
 
 #ifdef __cplusplus

@@ -72,6 +72,8 @@ SIGNATURES = {
     "wrs_mip_build": (_I, [_V, C.c_int64, C.c_int32, C.c_int32, C.c_int32, _V, C.c_size_t, _V]),
     "wrs_foveate": (_I, [_V, C.c_int64, _V, C.c_size_t, C.c_int32, C.c_int32, C.c_int32, _V,
                          C.c_float, C.c_float, C.c_int32, _V, C.c_int64, _V, _V]),
+    "wrs_push_foveated": (_I, [_V, _V, C.c_int64, _V, C.c_size_t, C.c_int32, _V, C.c_int32, C.c_float,
+                               C.c_float, _V, _V, _V]),
     "wrs_last_error": (C.c_char_p, []),
 }
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "wrs_device.cuh"
+#include "wrs_fov.cuh"
 
 namespace wrs {
 
@@ -99,12 +100,14 @@ __host__ __device__ __forceinline__ StageLayout stage_layout(int T, int K, int c
 // non-zero only to test the timeout path), then the lanes issue one bulk copy
 // per plane segment. The tile starts at pixel p0 (a multiple of T >= 256);
 // requires frame rows without padding, width % 4 == 0 and 16-byte aligned
-// frame and state planes.
+// frame and state planes. copy_frame = false leaves the frame segment to the
+// consumers (they foveate the frame into it themselves).
 template <int T>
 __device__ __forceinline__ void issue_tile_copies(const StreamDev& s, const FrameDev& f, int K,
                                                   int cs, bool resolve, const StageLayout& L,
                                                   uint8_t* stage, uint64_t* bar, int64_t p0,
-                                                  uint32_t extra_tx, int lane) {
+                                                  uint32_t extra_tx, int lane,
+                                                  bool copy_frame = true) {
   const int64_t rem_plane = s.plane - p0, rem_px = s.hw - p0;
   const uint32_t n = static_cast<uint32_t>(rem_plane < T ? rem_plane : T);  // plane entries (x64)
   const uint32_t np = static_cast<uint32_t>(rem_px < T ? rem_px : T);       // pixels (x4)
@@ -112,7 +115,7 @@ __device__ __forceinline__ void issue_tile_copies(const StreamDev& s, const Fram
   const int skip = s.literal ? 2 : 0;
   const int ncopy = 3 + K + (resolve ? (cs == 2 ? 2 * K : K) : 0);
   if (lane == 0) {
-    uint32_t bytes = 12u * np + 8u * n + 4u * K * n;
+    uint32_t bytes = (copy_frame ? 12u * np : 0u) + 8u * n + 4u * K * n;
     if (skip) bytes -= 4u * n + 4u * K * n;
     if (resolve) bytes += cs == 2 ? (4u * K * n + 8u * K * n) : 16u * K * n;
     mbar_arrive_expect_tx(bar, bytes + extra_tx);
@@ -121,6 +124,7 @@ __device__ __forceinline__ void issue_tile_copies(const StreamDev& s, const Fram
   const int64_t pl = s.plane;
   for (int c = lane; c < ncopy; c += 32) {
     if (skip && (c == 2 || c == 3)) continue;
+    if (c == 0 && !copy_frame) continue;
     if (c == 0) {
       bulk_g2s(stage + L.frame, f.frame + 3 * p0, 12u * np, bar);
     } else if (c == 1) {
@@ -176,7 +180,6 @@ __device__ __forceinline__ int compute_tile(const StreamDev& s, const FrameDev& 
   src.W = reinterpret_cast<const float*>(st + L.W);
   src.P = reinterpret_cast<const float*>(st + L.P);
   src.key = reinterpret_cast<const float*>(st + L.key);
-  src.idx = nullptr;
   src.wt = reinterpret_cast<const float*>(st + L.wt);
   src.col = st + L.col;
   src.stride = T;
@@ -193,6 +196,25 @@ __device__ __forceinline__ int compute_tile(const StreamDev& s, const FrameDev& 
 }
 
 // Adds a warp's counts to a running total: one atomic per warp.
+// As compute_tile, with the thread's PX pixels of the frame foveated from
+// `fv` into the stage's frame segment first (the producer copied no frame);
+// each thread writes and then reads only its own pixels there.
+template <int KT, bool F16, int PX, int T, bool LIT, int FILTER>
+__device__ __forceinline__ int compute_tile_fov(const StreamDev& s, const FrameDev& f,
+                                                const FovDev& fv, const StageLayout& L,
+                                                uint8_t* st, const float* u, int64_t p0,
+                                                float d_f, int tid) {
+  const int tl = tid * PX;
+  const int64_t p = p0 + tl;
+  if (p >= s.hw) return 0;
+  int y, x;
+  row_col(s, static_cast<int>(p), y, x);
+  float* fr = reinterpret_cast<float*>(st + L.frame) + 3 * tl;
+#pragma unroll
+  for (int i = 0; i < PX; ++i) fov_pixel<FILTER>(fv, f.gx, f.gy, x + i, y, fr + 3 * i);
+  return compute_tile<KT, F16, PX, T, LIT>(s, f, L, st, u, p0, d_f, tid);
+}
+
 __device__ __forceinline__ void add_warp_count(unsigned long long* total, int count, int lane) {
   const unsigned c = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(count));
   if (lane == 0 && c != 0) atomicAdd(total, static_cast<unsigned long long>(c));

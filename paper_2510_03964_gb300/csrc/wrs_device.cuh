@@ -363,7 +363,6 @@ struct Src {
   const float* W;
   const float* P;
   const float* key;
-  const uint32_t* idx;  // read only by the copying (reprojection) form
   const float* wt;
   const void* col;
   int64_t stride;
@@ -374,7 +373,7 @@ struct Src {
 
 __device__ __forceinline__ Src global_src(const StreamDev& s, const FrameDev& f, int p0, bool vec) {
   Src r;
-  r.W = s.W; r.P = s.P; r.key = s.key; r.idx = s.idx; r.wt = s.wt; r.col = s.col;
+  r.W = s.W; r.P = s.P; r.key = s.key; r.wt = s.wt; r.col = s.col;
   r.stride = s.plane;
   r.at = p0;
   r.frame = nullptr;
@@ -442,13 +441,10 @@ __device__ __forceinline__ void store_rgb(float* dst, const float (&o)[N][3]) {
 // group lies in one row and src.frame / f.out take vector accesses; otherwise
 // every pixel is addressed on its own (and may lie past the end of the image).
 // FOV: a flush map is present (f.fov != null); without one the flush logic is
-// compiled out. COPY: `src` is another buffer (the previous frame's state,
-// gathered by reprojection), so every slot is written to the global planes,
-// carried ones included; pre_flush drops the history of every pixel of the
-// group (a rejected reprojection).
-template <int KT, bool F16, int PX, bool VEC, bool FOV, bool COPY = false>
+// compiled out.
+template <int KT, bool F16, int PX, bool VEC, bool FOV>
 __device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f, int p0,
-                                          const Src& src, float d_f, bool pre_flush = false) {
+                                          const Src& src, float d_f) {
   const int K = KT > 0 ? KT : s.K;
   const int64_t pl = s.plane;
   const int64_t ss = src.stride;
@@ -495,8 +491,7 @@ __device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f,
 
   bool flush[PX];
 #pragma unroll
-  for (int i = 0; i < PX; ++i)
-    flush[i] = valid[i] && (pre_flush || (FOV && f.fov[p0 + i] == 0xFFu));
+  for (int i = 0; i < PX; ++i) flush[i] = FOV && valid[i] && f.fov[p0 + i] == 0xFFu;
 
   // uniforms: one Philox block per 4 consecutive pixels, word p mod 4 (PX divides
   // 4 and p0 % PX == 0, so the group never straddles two blocks)
@@ -629,37 +624,6 @@ __device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f,
   // stores: running sums, the replaced slot, rescaled keys, flushed slots
   store_f<PX>(s.W + p0, Wv);
   store_f<PX>(s.P + p0, Pv);
-  if constexpr (COPY) {
-#pragma unroll
-    for (int i = 0; i < PX; ++i) {
-      if (!valid[i]) continue;
-      const int64_t p = p0 + i;
-      for (int j = 0; j < K; ++j) {
-        if (repl[i] && j == jm[i]) {
-          s.key[j * pl + p] = ks[i];
-          s.idx[j * pl + p] = f.t;
-          store_slot<F16>(s.wt, s.col, K, j, pl, p, w[i], rgb[i][0], rgb[i][1], rgb[i][2]);
-        } else if (flush[i]) {
-          s.key[j * pl + p] = kInf;
-          s.idx[j * pl + p] = kEmpty;
-          store_slot<F16>(s.wt, s.col, K, j, pl, p, 0.0f, 0.0f, 0.0f, 0.0f);
-        } else {
-          // carried: the same slot of the gathered history
-          float kj = src.key[j * ss + sa + i];
-          if (rescale[i] && kj != kInf) kj = fminf(fmul(kj, kPScale), kFltMax);
-          s.key[j * pl + p] = kj;
-          s.idx[j * pl + p] = src.idx[j * ss + sa + i];
-          float a[1], r[1], g[1], b[1];
-          load_slot<F16, 1>(src.wt, src.col, K, j, ss, sa + i, a, r, g, b);
-          store_slot<F16>(s.wt, s.col, K, j, pl, p, a[0], r[0], g[0], b[0]);
-        }
-      }
-    }
-    int replaced = 0;
-#pragma unroll
-    for (int i = 0; i < PX; ++i) replaced += repl[i] ? 1 : 0;
-    return replaced;
-  }
 #pragma unroll
   for (int i = 0; i < PX; ++i) {
     if (!valid[i]) continue;
@@ -696,10 +660,9 @@ __device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f,
 // sample; W <- W' + w. One slot (K = 1), no key and no bias product: the P
 // and key planes are neither read nor written. Same frame, weight, uniform,
 // resolve and store code as the key race.
-template <bool F16, int PX, bool VEC, bool FOV, bool COPY = false>
+template <bool F16, int PX, bool VEC, bool FOV>
 __device__ __forceinline__ int push_group_literal(const StreamDev& s, const FrameDev& f, int p0,
-                                                  const Src& src, float d_f,
-                                                  bool pre_flush = false) {
+                                                  const Src& src, float d_f) {
   const int64_t pl = s.plane;
   const int64_t ss = src.stride;
   const int64_t sa = src.at;
@@ -741,8 +704,7 @@ __device__ __forceinline__ int push_group_literal(const StreamDev& s, const Fram
   }
   bool flush[PX];
 #pragma unroll
-  for (int i = 0; i < PX; ++i)
-    flush[i] = valid[i] && (pre_flush || (FOV && f.fov[p0 + i] == 0xFFu));
+  for (int i = 0; i < PX; ++i) flush[i] = FOV && valid[i] && f.fov[p0 + i] == 0xFFu;
   static_assert(4 % PX == 0, "pixels per thread must divide 4");
   float u[PX];
   if (src.u != nullptr) {
@@ -824,18 +786,6 @@ __device__ __forceinline__ int push_group_literal(const StreamDev& s, const Fram
     }
   }
   store_f<PX>(s.W + p0, Wv);
-  if constexpr (COPY) {
-    // the slot is always written: the new sample, or the gathered resident
-#pragma unroll
-    for (int i = 0; i < PX; ++i) {
-      if (!valid[i] || take[i]) continue;
-      const int64_t p = p0 + i;
-      s.idx[p] = src.idx[sa + i];
-      float a[1], r[1], g[1], b[1];
-      load_slot<F16, 1>(src.wt, src.col, 1, 0, ss, sa + i, a, r, g, b);
-      store_slot<F16>(s.wt, s.col, 1, 0, pl, p, a[0], r[0], g[0], b[0]);
-    }
-  }
   int taken = 0;
 #pragma unroll
   for (int i = 0; i < PX; ++i) {

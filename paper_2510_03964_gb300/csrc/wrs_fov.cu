@@ -22,7 +22,11 @@
 #include <cmath>
 #include <cstring>
 
+#include "wrs_fov.cuh"
 #include "wrs_internal.h"
+
+using wrs::FovDev;
+using wrs::MipLevelDev;
 
 namespace {
 
@@ -30,7 +34,8 @@ constexpr int kMipThreads = 256;
 constexpr int kTilePx = 2048;          // pixels per CTA strip: 2^M rows x (2048 >> M) columns
 constexpr int kFovThreads = 256;
 
-struct MipLevelDev {
+// Writable view of a stored level, for the build.
+struct MipLevelOut {
   float4* texels;
   int32_t wb, hb;
 };
@@ -40,20 +45,16 @@ struct MipArgs {
   int64_t pitch;
   int32_t width, height;
   int32_t top;                          // highest level built, 1..WRS_MAX_MIP_LEVELS-1
-  MipLevelDev lev[WRS_MAX_MIP_LEVELS];  // [0] unused
+  MipLevelOut lev[WRS_MAX_MIP_LEVELS];  // [0] unused
 };
 
 struct FovArgs {
-  const float* img;
-  int64_t pitch;
+  FovDev fv;
   float* frame;
   int64_t frame_pitch;
   uint8_t* ring;
   int32_t width, height;
-  int32_t nradii;
   float gx, gy;
-  float r2[WRS_MAX_MIP_LEVELS - 1];
-  MipLevelDev lev[WRS_MAX_MIP_LEVELS];  // [0] unused
 };
 
 __device__ __forceinline__ int32_t block_extent(int32_t n, int32_t i, int L) {
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(kMipThreads) mip_kernel(MipArgs a) {
     const int lw = TW >> L;
     const int lh = TH >> L;
     const int n = lw * lh;
-    const MipLevelDev lv = a.lev[L];
+    const MipLevelOut lv = a.lev[L];
     for (int i = tid; i < n; i += kMipThreads) {
       const int r = i / lw, c = i - r * lw;
       const float* p0 = prev + ((2 * r) * prev_w + 2 * c) * 3;
@@ -154,61 +155,6 @@ __global__ void __launch_bounds__(kMipThreads) mip_kernel(MipArgs a) {
   }
 }
 
-__device__ __forceinline__ void texel_coord(int32_t i, int L, int32_t nb, int32_t* i0, int32_t* i1,
-                                            float* f) {
-  const float inv_b = __int_as_float((127 - L) << 23);  // 2^-L, exact
-  float u = __fsub_rn(__fmul_rn(__fadd_rn((float)i, 0.5f), inv_b), 0.5f);
-  u = fminf(fmaxf(u, 0.0f), (float)(nb - 1));
-  const float fl = floorf(u);
-  *i0 = (int32_t)fl;
-  *i1 = *i0 + 1 < nb ? *i0 + 1 : nb - 1;
-  *f = __fsub_rn(u, fl);
-}
-
-__device__ __forceinline__ float lerp2(float a, float b, float one_minus_f, float f) {
-  return __fadd_rn(__fmul_rn(a, one_minus_f), __fmul_rn(b, f));
-}
-
-// Colour and ring level of pixel (x, y).
-template <int FILTER>
-__device__ __forceinline__ int fov_pixel(const FovArgs& a, int32_t x, int32_t y, float* rgb) {
-  const float dx = __fsub_rn(__fadd_rn((float)x, 0.5f), a.gx);
-  const float dy = __fsub_rn(__fadd_rn((float)y, 0.5f), a.gy);
-  const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-  int L = 0;
-#pragma unroll
-  for (int i = 0; i < WRS_MAX_MIP_LEVELS - 1; ++i)
-    if (i < a.nradii) L += d2 > a.r2[i];
-  if (L == 0) {
-    const float* s = a.img + (int64_t)y * a.pitch + 3 * (int64_t)x;
-    rgb[0] = __ldg(s);
-    rgb[1] = __ldg(s + 1);
-    rgb[2] = __ldg(s + 2);
-  } else {
-    const MipLevelDev lv = a.lev[L];
-    if (FILTER == WRS_FILTER_BOX) {
-      const float4 t = __ldg(lv.texels + (int64_t)(y >> L) * lv.wb + (x >> L));
-      rgb[0] = t.x;
-      rgb[1] = t.y;
-      rgb[2] = t.z;
-    } else {
-      int32_t x0, x1, y0, y1;
-      float fx, fy;
-      texel_coord(x, L, lv.wb, &x0, &x1, &fx);
-      texel_coord(y, L, lv.hb, &y0, &y1, &fy);
-      const float4 t00 = __ldg(lv.texels + (int64_t)y0 * lv.wb + x0);
-      const float4 t01 = __ldg(lv.texels + (int64_t)y0 * lv.wb + x1);
-      const float4 t10 = __ldg(lv.texels + (int64_t)y1 * lv.wb + x0);
-      const float4 t11 = __ldg(lv.texels + (int64_t)y1 * lv.wb + x1);
-      const float gx_ = __fsub_rn(1.0f, fx), gy_ = __fsub_rn(1.0f, fy);
-      rgb[0] = lerp2(lerp2(t00.x, t01.x, gx_, fx), lerp2(t10.x, t11.x, gx_, fx), gy_, fy);
-      rgb[1] = lerp2(lerp2(t00.y, t01.y, gx_, fx), lerp2(t10.y, t11.y, gx_, fx), gy_, fy);
-      rgb[2] = lerp2(lerp2(t00.z, t01.z, gx_, fx), lerp2(t10.z, t11.z, gx_, fx), gy_, fy);
-    }
-  }
-  return L;
-}
-
 // One pixel per thread (any width, pitch and alignment).
 template <int FILTER>
 __global__ void __launch_bounds__(kFovThreads) foveate_kernel(FovArgs a) {
@@ -218,7 +164,7 @@ __global__ void __launch_bounds__(kFovThreads) foveate_kernel(FovArgs a) {
     const int32_t y = (int32_t)(p / a.width);
     const int32_t x = (int32_t)(p - (int64_t)y * a.width);
     float rgb[3];
-    const int L = fov_pixel<FILTER>(a, x, y, rgb);
+    const int L = wrs::fov_pixel<FILTER>(a.fv, a.gx, a.gy, x, y, rgb);
     float* o = a.frame + (int64_t)y * a.frame_pitch + 3 * (int64_t)x;
     o[0] = rgb[0];
     o[1] = rgb[1];
@@ -242,7 +188,7 @@ __global__ void __launch_bounds__(kFovThreads) foveate4_kernel(FovArgs a) {
     uint32_t lv = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-      lv |= (uint32_t)fov_pixel<FILTER>(a, x0 + i, y, rgb + 3 * i) << (8 * i);
+      lv |= (uint32_t)wrs::fov_pixel<FILTER>(a.fv, a.gx, a.gy, x0 + i, y, rgb + 3 * i) << (8 * i);
     float4* o = reinterpret_cast<float4*>(a.frame + (int64_t)y * a.frame_pitch + 3 * (int64_t)x0);
     o[0] = make_float4(rgb[0], rgb[1], rgb[2], rgb[3]);
     o[1] = make_float4(rgb[4], rgb[5], rgb[6], rgb[7]);
@@ -261,7 +207,8 @@ int check_image(int32_t width, int32_t height) {
   return WRS_OK;
 }
 
-void fill_levels(const wrs_mip_layout& L, const void* base, MipLevelDev* lev) {
+template <typename Level>
+void fill_levels(const wrs_mip_layout& L, const void* base, Level* lev) {
   for (int l = 1; l < L.levels; ++l) {
     lev[l].texels = reinterpret_cast<float4*>(const_cast<uint8_t*>(
         static_cast<const uint8_t*>(base) + L.offset[l]));
@@ -344,46 +291,60 @@ extern "C" int wrs_mip_build(const float* d_img, int64_t pitch, int32_t width, i
   return e == cudaSuccess ? WRS_OK : wrs_cuda_fail(e, "wrs_mip_build: launch");
 }
 
-extern "C" int wrs_foveate(const float* d_img, int64_t pitch, const void* d_mip, size_t mip_bytes,
-                           int32_t width, int32_t height, int32_t nradii, const float* radii,
-                           float gx, float gy, int32_t filter, float* d_frame,
-                           int64_t frame_pitch, uint8_t* d_ring, wrs_stream_t stream) {
-  wrs_clear_error();
+int wrs_fov_source(const float* d_img, int64_t pitch, const void* d_mip, size_t mip_bytes,
+                   int32_t width, int32_t height, int32_t nradii, const float* radii,
+                   int32_t filter, FovDev* out) {
   if (int rc = check_image(width, height)) return rc;
   if (nradii < 1 || nradii > WRS_MAX_MIP_LEVELS - 1 || !radii)
     return wrs_fail(WRS_ERR_ARG, "nradii must be in 1..%d with a radii array",
                     WRS_MAX_MIP_LEVELS - 1);
   if (filter != WRS_FILTER_BOX && filter != WRS_FILTER_BILINEAR)
     return wrs_fail(WRS_ERR_ARG, "filter must be WRS_FILTER_BOX or WRS_FILTER_BILINEAR");
-  if (!std::isfinite(gx) || !std::isfinite(gy)) return wrs_fail(WRS_ERR_ARG, "gaze must be finite");
-  if (!d_img || !d_frame || !aligned(d_img, 4) || !aligned(d_frame, 4))
-    return wrs_fail(WRS_ERR_ARG, "d_img and d_frame must be non-NULL and 4-byte aligned");
-  if (pitch < 3 * (int64_t)width || frame_pitch < 3 * (int64_t)width)
-    return wrs_fail(WRS_ERR_ARG, "pitches must be >= 3 * width");
+  if (!d_img || !aligned(d_img, 4)) return wrs_fail(WRS_ERR_ARG, "d_img is NULL or unaligned");
+  if (pitch < 3 * (int64_t)width)
+    return wrs_fail(WRS_ERR_ARG, "img_pitch_elems %lld is below 3 * width", (long long)pitch);
   if (!d_mip || !aligned(d_mip, 256))
     return wrs_fail(WRS_ERR_ARG, "d_mip is NULL or not 256-byte aligned");
-  FovArgs a{};
+  FovDev fv{};
   for (int i = 0; i < nradii; ++i) {
     if (!std::isfinite(radii[i]) || !(radii[i] > 0.0f) || (i > 0 && radii[i] < radii[i - 1]))
       return wrs_fail(WRS_ERR_ARG, "radii must be finite, positive and ascending");
-    a.r2[i] = radii[i] * radii[i];
+    fv.r2[i] = radii[i] * radii[i];
   }
   wrs_mip_layout L;
   if (int rc = wrs_mip_layout_get(width, height, nradii + 1, &L)) return rc;
   if ((int64_t)mip_bytes < L.total_bytes)
     return wrs_fail(WRS_ERR_BUDGET, "mip buffer holds %zu bytes, %d levels need %lld", mip_bytes,
                     nradii + 1, (long long)L.total_bytes);
-  a.img = d_img;
-  a.pitch = pitch;
+  fv.img = d_img;
+  fv.pitch = pitch;
+  fv.nradii = nradii;
+  fill_levels(L, d_mip, fv.lev);
+  *out = fv;
+  return WRS_OK;
+}
+
+extern "C" int wrs_foveate(const float* d_img, int64_t pitch, const void* d_mip, size_t mip_bytes,
+                           int32_t width, int32_t height, int32_t nradii, const float* radii,
+                           float gx, float gy, int32_t filter, float* d_frame,
+                           int64_t frame_pitch, uint8_t* d_ring, wrs_stream_t stream) {
+  wrs_clear_error();
+  if (!std::isfinite(gx) || !std::isfinite(gy)) return wrs_fail(WRS_ERR_ARG, "gaze must be finite");
+  if (!d_frame || !aligned(d_frame, 4))
+    return wrs_fail(WRS_ERR_ARG, "d_frame must be non-NULL and 4-byte aligned");
+  if (frame_pitch < 3 * (int64_t)width)
+    return wrs_fail(WRS_ERR_ARG, "pitches must be >= 3 * width");
+  FovArgs a{};
+  if (int rc = wrs_fov_source(d_img, pitch, d_mip, mip_bytes, width, height, nradii, radii, filter,
+                              &a.fv))
+    return rc;
   a.frame = d_frame;
   a.frame_pitch = frame_pitch;
   a.ring = d_ring;
   a.width = width;
   a.height = height;
-  a.nradii = nradii;
   a.gx = gx;
   a.gy = gy;
-  fill_levels(L, d_mip, a.lev);
   int sms = 0;
   if (int rc = device_sms(&sms)) return rc;
   const bool quad = width % 4 == 0 && frame_pitch % 4 == 0 && aligned(d_frame, 16) &&

@@ -5,6 +5,7 @@
 
 #include "wrs.h"
 #include "wrs_device.cuh"
+#include "wrs_fov.cuh"
 
 struct wrs_ctx {
   wrs_config cfg;
@@ -47,5 +48,14 @@ float wrs_delta(const wrs_config* c);
 wrs::StreamDev wrs_stream_dev(const wrs_ctx* x);
 cudaError_t wrs_init_planes(const wrs_ctx* x, uint8_t* base, cudaStream_t st);
 int wrs_effective_px(const wrs_ctx* x, const float* frame, int64_t pitch, const float* out);
+// Validates a foveation source (image, mip buffer, radii, filter) and fills fv.
+int wrs_fov_source(const float* d_img, int64_t pitch, const void* d_mip, size_t mip_bytes,
+                   int32_t width, int32_t height, int32_t nradii, const float* radii,
+                   int32_t filter, wrs::FovDev* fv);
+// The pipelined kernel foveating the frame as it reads it (filter: WRS_FILTER_*).
+cudaError_t wrs_launch_pipe_fov(const wrs::StreamDev& s, const wrs::FrameDev& f,
+                                const wrs::FovDev& fv, int filter, bool f16, int stages, int sms,
+                                int ctas_per_sm, uint32_t* status, uint64_t timeout_ns,
+                                cudaStream_t st);
 cudaError_t wrs_launch_push(const wrs::StreamDev& s, const wrs::FrameDev& f, int block, int px,
                             bool f16, cudaStream_t st);

@@ -399,6 +399,42 @@ extern "C" int wrs_push_frame(wrs_ctx* x, const float* d_frame, int64_t pitch, f
   return WRS_OK;
 }
 
+extern "C" int wrs_push_foveated(wrs_ctx* x, const float* d_img, int64_t img_pitch,
+                                 const void* d_mip, size_t mip_bytes, int32_t nradii,
+                                 const float* radii, int32_t filter, float gx, float gy,
+                                 const uint8_t* d_fov, float* d_out, wrs_stream_t stream) {
+  wrs_clear_error();
+  if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
+  if (x->cfg.width % 4 != 0)
+    return wrs_fail(WRS_ERR_ARG, "foveating on read needs width %% 4 == 0 (got %d)",
+                    x->cfg.width);
+  if (d_out && !aligned(d_out, 16)) return wrs_fail(WRS_ERR_ARG, "d_out must be 16-byte aligned");
+  if (!std::isfinite(gx) || !std::isfinite(gy))
+    return wrs_fail(WRS_ERR_ARG, "gaze must be finite");
+  wrs::FovDev fv;
+  if (int rc = wrs_fov_source(d_img, img_pitch, d_mip, mip_bytes, x->cfg.width, x->cfg.height,
+                              nradii, radii, filter, &fv))
+    return rc;
+  if (x->t == 0xFFFFFFFFu) return wrs_fail(WRS_ERR_STATE, "frame counter exhausted");
+  const StreamDev s = wrs_stream_dev(x);
+  FrameDev f;
+  f.frame = nullptr;  // the consumers foveate the frame into shared memory
+  f.pitch = 3 * static_cast<int64_t>(x->cfg.width);
+  f.fov = d_fov;
+  f.out = d_out;
+  f.gx = gx;
+  f.gy = gy;
+  f.t = x->t;
+  int px = x->pipe_px, stages = x->pipe_stages;
+  if (px != 1) wrs_default_pipe(x->cfg.K, x->cfg.color_fp16 != 0, &px, &stages);
+  cudaError_t e = wrs_launch_pipe_fov(s, f, fv, filter, x->cfg.color_fp16 != 0, stages, x->sms,
+                                      x->pipe_ctas, wrs_status_word(x), x->timeout_ns,
+                                      static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_foveated: launch");
+  x->t += 1;
+  return WRS_OK;
+}
+
 extern "C" int wrs_resolve(wrs_ctx* x, float* d_out, wrs_stream_t stream) {
   wrs_clear_error();
   if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");

@@ -23,6 +23,7 @@
 #include "wrs_device.cuh"
 #include "wrs_internal.h"
 
+using wrs::FovDev;
 using wrs::FrameDev;
 using wrs::StageLayout;
 using wrs::StreamDev;
@@ -44,10 +45,12 @@ constexpr int kPipeThreads = (kConsumerWarps + 1) * 32;
 // Warp-specialised: warps 0..7 compute (consumers, PX pixels per thread), warp 8
 // draws uniforms and issues copies (producer). Consumers and producer meet
 // only at the per-stage full/empty barriers, never at a block-wide barrier.
-template <int KT, bool F16, int PX, bool LIT>
+// FOVF >= 0: the frame is not copied but foveated by the consumers from `fv`
+// with filter FOVF (WRS_FILTER_*) as they compute; FOVF < 0: `fv` is unused.
+template <int KT, bool F16, int PX, bool LIT, int FOVF = -1>
 __global__ void __launch_bounds__(kPipeThreads, PX == 1 ? 2 : 1)
     pipe_kernel(const __grid_constant__ StreamDev s, const __grid_constant__ FrameDev f,
-                const PipeArgs a) {
+                const PipeArgs a, const __grid_constant__ FovDev fv) {
   extern __shared__ __align__(128) uint8_t smem[];
   constexpr int T = kConsumerWarps * 32 * PX;
   constexpr int cs = F16 ? 2 : 4;
@@ -73,13 +76,17 @@ __global__ void __launch_bounds__(kPipeThreads, PX == 1 ? 2 : 1)
                             wrs::draw_tile_uniforms_warp<T>(s, f, p0, u, ln);
                             __syncwarp();
                             wrs::issue_tile_copies<T>(s, f, K, cs, resolve, L, st, full, p0,
-                                                      a.extra_tx, ln);
+                                                      a.extra_tx, ln, FOVF < 0);
                           });
   } else {
     const float d_f = wrs::fovea_density(s);
-    wrs::consume(r, my_tiles, a.timeout_ns, lane, [&](int it, const uint8_t* st, const float* u) {
+    wrs::consume(r, my_tiles, a.timeout_ns, lane, [&](int it, uint8_t* st, const float* u) {
       const int64_t p0 = static_cast<int64_t>(first + it * step) * T;
-      replaced += wrs::compute_tile<KT, F16, PX, T, LIT>(s, f, L, st, u, p0, d_f, tid);
+      if constexpr (FOVF >= 0)
+        replaced +=
+            wrs::compute_tile_fov<KT, F16, PX, T, LIT, FOVF>(s, f, fv, L, st, u, p0, d_f, tid);
+      else
+        replaced += wrs::compute_tile<KT, F16, PX, T, LIT>(s, f, L, st, u, p0, d_f, tid);
     });
   }
   __syncthreads();
@@ -90,9 +97,9 @@ __global__ void __launch_bounds__(kPipeThreads, PX == 1 ? 2 : 1)
   }
 }
 
-template <int KT, bool F16, int PX, bool LIT = false>
+template <int KT, bool F16, int PX, bool LIT = false, int FOVF = -1>
 cudaError_t launch_pipe_t(const StreamDev& s, const FrameDev& f, PipeArgs a, int sms,
-                          int ctas_per_sm, cudaStream_t st) {
+                          int ctas_per_sm, cudaStream_t st, const FovDev& fv = FovDev{}) {
   constexpr int T = kConsumerWarps * 32 * PX;
   const StageLayout L = wrs::stage_layout(T, s.K, F16 ? 2 : 4, a.resolve != 0);
   const size_t smem = wrs::ring_bytes(L.bytes, T, a.stages);
@@ -103,22 +110,35 @@ cudaError_t launch_pipe_t(const StreamDev& s, const FrameDev& f, PipeArgs a, int
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (smem > configured[dev]) {
-    e = cudaFuncSetAttribute(pipe_kernel<KT, F16, PX, LIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smem));
+    e = cudaFuncSetAttribute(pipe_kernel<KT, F16, PX, LIT, FOVF>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     configured[dev] = smem;
   }
   int fit = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, pipe_kernel<KT, F16, PX, LIT>, kPipeThreads,
-                                                    smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, pipe_kernel<KT, F16, PX, LIT, FOVF>,
+                                                    kPipeThreads, smem);
   if (e != cudaSuccess) return e;
   if (fit < 1) return cudaErrorInvalidConfiguration;
   const int per_sm = ctas_per_sm > 0 && ctas_per_sm < fit ? ctas_per_sm : fit;
   a.ntiles = static_cast<int>((static_cast<int64_t>(s.hw) + T - 1) / T);
   const int64_t want = static_cast<int64_t>(sms) * per_sm;
   const int grid = static_cast<int>(a.ntiles < want ? a.ntiles : want);
-  pipe_kernel<KT, F16, PX, LIT><<<grid, kPipeThreads, smem, st>>>(s, f, a);
+  pipe_kernel<KT, F16, PX, LIT, FOVF><<<grid, kPipeThreads, smem, st>>>(s, f, a, fv);
   return cudaGetLastError();
+}
+
+// The foveating form: one pixel per thread (the default tile), K = 4, 8 or
+// any other through the generic instantiation, and the literal rule.
+template <bool F16, int FILTER>
+cudaError_t launch_pipe_fov_k(const StreamDev& s, const FrameDev& f, const FovDev& fv,
+                              const PipeArgs& a, int sms, int ctas, cudaStream_t st) {
+  if (s.literal) return launch_pipe_t<1, F16, 1, true, FILTER>(s, f, a, sms, ctas, st, fv);
+  switch (s.K) {
+    case 4: return launch_pipe_t<4, F16, 1, false, FILTER>(s, f, a, sms, ctas, st, fv);
+    case 8: return launch_pipe_t<8, F16, 1, false, FILTER>(s, f, a, sms, ctas, st, fv);
+    default: return launch_pipe_t<0, F16, 1, false, FILTER>(s, f, a, sms, ctas, st, fv);
+  }
 }
 
 template <int KT, bool F16, bool LIT = false>
@@ -156,6 +176,23 @@ bool wrs_pipe_supported(const wrs_ctx* x, const float* frame, int64_t pitch, con
   const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
   return x->cfg.width % 4 == 0 && pitch == 3 * static_cast<int64_t>(x->cfg.width) && al(frame) &&
          (out == nullptr || al(out));
+}
+
+cudaError_t wrs_launch_pipe_fov(const StreamDev& s, const FrameDev& f, const FovDev& fv, int filter,
+                                bool f16, int stages, int sms, int ctas_per_sm, uint32_t* status,
+                                uint64_t timeout_ns, cudaStream_t st) {
+  PipeArgs a;
+  a.stages = stages;
+  a.ntiles = 0;
+  a.resolve = f.out != nullptr ? 1 : 0;
+  a.status = status;
+  a.timeout_ns = timeout_ns;
+  a.extra_tx = 0;
+  if (filter == WRS_FILTER_BOX)
+    return f16 ? launch_pipe_fov_k<true, WRS_FILTER_BOX>(s, f, fv, a, sms, ctas_per_sm, st)
+               : launch_pipe_fov_k<false, WRS_FILTER_BOX>(s, f, fv, a, sms, ctas_per_sm, st);
+  return f16 ? launch_pipe_fov_k<true, WRS_FILTER_BILINEAR>(s, f, fv, a, sms, ctas_per_sm, st)
+             : launch_pipe_fov_k<false, WRS_FILTER_BILINEAR>(s, f, fv, a, sms, ctas_per_sm, st);
 }
 
 cudaError_t wrs_launch_pipe(const StreamDev& s, const FrameDev& f, bool f16, int px, int stages,

@@ -6,8 +6,9 @@
 // cannot run in place: it reads one state buffer and writes every slot to the
 // other, and the buffers swap roles afterwards.
 //
-// One pixel per thread: under a pan the gathered rows are the current rows
-// shifted, so neighbouring threads still read neighbouring addresses.
+// One pixel per thread, its whole history held in registers: under a pan the
+// gathered rows are the current rows shifted, so neighbouring threads still
+// read neighbouring addresses.
 #include <cmath>
 
 #include "wrs_internal.h"
@@ -26,7 +27,229 @@ struct ReprojDev {
   float tol;
 };
 
-template <bool F16, bool LIT, bool FOV>
+// Where pixel p's history comes from: the previous frame's pixel containing
+// the centre moved back by the motion vector; `ok` is false when that point
+// is off screen or the depth test rejects it (q is then p, a valid address).
+__device__ __forceinline__ int64_t source_pixel(const StreamDev& s, const ReprojDev& r, int64_t p,
+                                                int x, int y, float dp, bool& ok) {
+  float mx = 0.0f, my = 0.0f;
+  if (r.motion != nullptr) {
+    const float2 m = r.motion[p];
+    mx = m.x;
+    my = m.y;
+  }
+  const float cx = __fsub_rn(__fadd_rn(static_cast<float>(x), 0.5f), mx);
+  const float cy = __fsub_rn(__fadd_rn(static_cast<float>(y), 0.5f), my);
+  ok = cx >= 0.0f && cx < static_cast<float>(s.width) && cy >= 0.0f &&
+       cy < static_cast<float>(s.height);  // false for NaN
+  int64_t q = p;
+  if (ok) q = static_cast<int64_t>(floorf(cy)) * s.width + static_cast<int64_t>(floorf(cx));
+  if (ok && r.depth != nullptr) {
+    const float dq = r.prev_depth[q];
+    if (fabsf(__fsub_rn(dq, dp)) > __fmul_rn(r.tol, dp)) ok = false;
+  }
+  return q;
+}
+
+// The key race for one pixel with its history gathered into registers: every
+// load of the pixel (frame, motion, depths, then the whole source reservoir)
+// is issued before any of it is used, and the arithmetic is the in-place
+// update's, step for step (push_group): Eq. (full-temporal-bias) factor from
+// the history's resolved colour, Eq. (temporal-bias), the key race, the fused
+// resolve, then every slot written to the other buffer. KT >= K bounds the
+// register arrays.
+template <int KT, bool F16, bool FOV>
+__device__ __forceinline__ int reproject_keys(const StreamDev& cur, const StreamDev& prev,
+                                              const FrameDev& f, const ReprojDev& r, int64_t p,
+                                              float d_f) {
+  using namespace wrs;
+  const int K = cur.K;
+  const int64_t pl = cur.plane;
+  int y, x;
+  row_col(cur, static_cast<int>(p), y, x);
+  const float* fp = f.frame + static_cast<int64_t>(y) * f.pitch + 3 * x;
+  float rgb[3] = {fp[0], fp[1], fp[2]};
+  const float dp = r.depth != nullptr ? r.depth[p] : 0.0f;
+  bool flush = FOV && f.fov[p] == 0xFFu;
+
+  const uint4 blk = philox4x32_10(make_uint4(static_cast<uint32_t>(p) >> 2, f.t, cur.stream_id, 0u),
+                                  cur.seed_lo, cur.seed_hi);
+  const float u = unit_uniform(word(blk, static_cast<int>(p) & 3));
+  const float w = pixel_weight(cur, d_f, x, y, f.gx, f.gy);
+  const float k = fdiv(-log_pos(u), w);
+
+  bool ok;
+  const int64_t q = source_pixel(cur, r, p, x, y, dp, ok);
+  float W = prev.W[q], P = prev.P[q];
+  float key[KT], a[KT], cr[KT], cg[KT], cb[KT];
+  uint32_t id[KT];
+#pragma unroll
+  for (int j = 0; j < KT; ++j) {
+    if (j < K) {
+      key[j] = prev.key[j * pl + q];
+      id[j] = prev.idx[j * pl + q];
+      float a1[1], r1[1], g1[1], b1[1];
+      load_slot<F16, 1>(prev.wt, prev.col, K, j, pl, q, a1, r1, g1, b1);
+      a[j] = a1[0]; cr[j] = r1[0]; cg[j] = g1[0]; cb[j] = b1[0];
+    } else {
+      key[j] = kInf; id[j] = kEmpty; a[j] = cr[j] = cg[j] = cb[j] = 0.0f;
+    }
+  }
+  flush = flush || !ok;
+
+  float gl = 1.0f;
+  if (cur.bias == 2) {
+    float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f, dn = 0.0f;
+#pragma unroll
+    for (int j = 0; j < KT; ++j) {
+      if (j < K) {
+        n0 = __fmaf_rn(a[j], cr[j], n0);
+        n1 = __fmaf_rn(a[j], cg[j], n1);
+        n2 = __fmaf_rn(a[j], cb[j], n2);
+        dn = fadd(dn, a[j]);
+      }
+    }
+    if (!flush && W > 0.0f) {
+      gl = lightness_factor(n0, n1, n2, dn, rgb);
+      if (gl <= 0.0f) flush = true;
+    }
+  }
+  if (flush) { W = 0.0f; P = 1.0f; }
+  bool rescale;
+  const float ks = bias_and_sum(cur.bias, w, k, W, P, rescale, gl);
+
+  float kmax = -1.0f;
+  int jm = 0;
+#pragma unroll
+  for (int j = 0; j < KT; ++j) {
+    if (j < K) {
+      const float kj = race_key(key[j], flush, rescale);
+      if (kj > kmax) { kmax = kj; jm = j; }
+    }
+  }
+  const bool repl = ks < kmax;
+  const float c0 = stored_colour<F16>(rgb[0]), c1 = stored_colour<F16>(rgb[1]),
+              c2 = stored_colour<F16>(rgb[2]);
+
+  if (f.out != nullptr) {
+    float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f, dn = 0.0f;
+#pragma unroll
+    for (int j = 0; j < KT; ++j) {
+      if (j < K) {
+        float aa = a[j], rr = cr[j], gg = cg[j], bb = cb[j];
+        if (flush) { aa = 0.0f; rr = gg = bb = 0.0f; }
+        if (repl && jm == j) { aa = w; rr = c0; gg = c1; bb = c2; }
+        n0 = __fmaf_rn(aa, rr, n0);
+        n1 = __fmaf_rn(aa, gg, n1);
+        n2 = __fmaf_rn(aa, bb, n2);
+        dn = fadd(dn, aa);
+      }
+    }
+    const float inv = dn > 0.0f ? __frcp_rn(dn) : 0.0f;
+    float* o = f.out + p * 3;
+    o[0] = fmul(n0, inv);
+    o[1] = fmul(n1, inv);
+    o[2] = fmul(n2, inv);
+  }
+
+  cur.W[p] = W;
+  cur.P[p] = P;
+#pragma unroll
+  for (int j = 0; j < KT; ++j) {
+    if (j >= K) continue;
+    if (repl && j == jm) {
+      cur.key[j * pl + p] = ks;
+      cur.idx[j * pl + p] = f.t;
+      store_slot<F16>(cur.wt, cur.col, K, j, pl, p, w, rgb[0], rgb[1], rgb[2]);
+    } else if (flush) {
+      cur.key[j * pl + p] = kInf;
+      cur.idx[j * pl + p] = kEmpty;
+      store_slot<F16>(cur.wt, cur.col, K, j, pl, p, 0.0f, 0.0f, 0.0f, 0.0f);
+    } else {
+      float kj = key[j];
+      if (rescale && kj != kInf) kj = fminf(fmul(kj, kPScale), kFltMax);
+      cur.key[j * pl + p] = kj;
+      cur.idx[j * pl + p] = id[j];
+      store_slot<F16>(cur.wt, cur.col, K, j, pl, p, a[j], cr[j], cg[j], cb[j]);
+    }
+  }
+  return repl ? 1 : 0;
+}
+
+// The literal n = 1 rule (Alg. 2 with Eq. (temporal-bias)) for one pixel with
+// its gathered history, step for step as push_group_literal; the key and bias
+// planes are neither read nor written.
+template <bool F16, bool FOV>
+__device__ __forceinline__ int reproject_literal(const StreamDev& cur, const StreamDev& prev,
+                                                 const FrameDev& f, const ReprojDev& r, int64_t p,
+                                                 float d_f) {
+  using namespace wrs;
+  const int64_t pl = cur.plane;
+  int y, x;
+  row_col(cur, static_cast<int>(p), y, x);
+  const float* fp = f.frame + static_cast<int64_t>(y) * f.pitch + 3 * x;
+  float rgb[3] = {fp[0], fp[1], fp[2]};
+  const float dp = r.depth != nullptr ? r.depth[p] : 0.0f;
+  bool flush = FOV && f.fov[p] == 0xFFu;
+  const uint4 blk = philox4x32_10(make_uint4(static_cast<uint32_t>(p) >> 2, f.t, cur.stream_id, 0u),
+                                  cur.seed_lo, cur.seed_hi);
+  const float u = unit_uniform(word(blk, static_cast<int>(p) & 3));
+  const float w = pixel_weight(cur, d_f, x, y, f.gx, f.gy);
+
+  bool ok;
+  const int64_t q = source_pixel(cur, r, p, x, y, dp, ok);
+  float W = prev.W[q];
+  const uint32_t id0 = prev.idx[q];
+  float a1[1], r1[1], g1[1], b1[1];
+  load_slot<F16, 1>(prev.wt, prev.col, 1, 0, pl, q, a1, r1, g1, b1);
+  flush = flush || !ok;
+
+  float gl = 1.0f;
+  if (cur.bias == 2 && !flush && W > 0.0f) {
+    gl = lightness_factor(__fmaf_rn(a1[0], r1[0], 0.0f), __fmaf_rn(a1[0], g1[0], 0.0f),
+                          __fmaf_rn(a1[0], b1[0], 0.0f), fadd(0.0f, a1[0]), rgb);
+    if (gl <= 0.0f) flush = true;
+  }
+  if (flush) W = 0.0f;
+  if (cur.bias && W > 0.0f) {
+    float fb = fdiv(W, fadd(W, w));
+    if (cur.bias == 2) fb = fmul(fb, gl);
+    W = fmul(W, fb);
+  }
+  const float tot = fadd(W, w);
+  const bool take = !(fmul(u, tot) <= W);  // Alg. 2: R1 kept on <=
+  W = tot;
+
+  if (f.out != nullptr) {
+    float aa = a1[0], rr = r1[0], gg = g1[0], bb = b1[0];
+    if (take) {
+      aa = w;
+      rr = stored_colour<F16>(rgb[0]);
+      gg = stored_colour<F16>(rgb[1]);
+      bb = stored_colour<F16>(rgb[2]);
+    }
+    const float n0 = __fmaf_rn(aa, rr, 0.0f), n1 = __fmaf_rn(aa, gg, 0.0f),
+                n2 = __fmaf_rn(aa, bb, 0.0f);
+    const float den = fadd(0.0f, aa);
+    const float inv = den > 0.0f ? __frcp_rn(den) : 0.0f;
+    float* o = f.out + p * 3;
+    o[0] = fmul(n0, inv);
+    o[1] = fmul(n1, inv);
+    o[2] = fmul(n2, inv);
+  }
+  cur.W[p] = W;
+  if (take) {
+    cur.idx[p] = f.t;
+    store_slot<F16>(cur.wt, cur.col, 1, 0, pl, p, w, rgb[0], rgb[1], rgb[2]);
+  } else {
+    cur.idx[p] = id0;
+    store_slot<F16>(cur.wt, cur.col, 1, 0, pl, p, a1[0], r1[0], g1[0], b1[0]);
+  }
+  return take ? 1 : 0;
+}
+
+// KT > 0: the key race with K <= KT slots; KT == 0: the literal rule.
+template <int KT, bool F16, bool FOV>
 __global__ void __launch_bounds__(kThreads) reproject_kernel(const __grid_constant__ StreamDev cur,
                                                              const __grid_constant__ StreamDev prev,
                                                              const __grid_constant__ FrameDev f,
@@ -35,43 +258,13 @@ __global__ void __launch_bounds__(kThreads) reproject_kernel(const __grid_consta
   if (threadIdx.x == 0) block_replaced = 0;
   __syncthreads();
   const float d_f = wrs::fovea_density(cur);
-  const float fw = static_cast<float>(cur.width), fh = static_cast<float>(cur.height);
   int replaced = 0;
   for (int64_t p = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; p < cur.hw;
        p += static_cast<int64_t>(gridDim.x) * kThreads) {
-    int y, x;
-    wrs::row_col(cur, static_cast<int>(p), y, x);
-    float mx = 0.0f, my = 0.0f;
-    if (r.motion != nullptr) {
-      const float2 m = r.motion[p];
-      mx = m.x;
-      my = m.y;
-    }
-    const float cx = __fsub_rn(__fadd_rn(static_cast<float>(x), 0.5f), mx);
-    const float cy = __fsub_rn(__fadd_rn(static_cast<float>(y), 0.5f), my);
-    bool ok = cx >= 0.0f && cx < fw && cy >= 0.0f && cy < fh;  // false for NaN
-    int64_t q = p;
-    if (ok) q = static_cast<int64_t>(floorf(cy)) * cur.width + static_cast<int64_t>(floorf(cx));
-    if (ok && r.depth != nullptr) {
-      const float dp = r.depth[p], dq = r.prev_depth[q];
-      if (fabsf(__fsub_rn(dq, dp)) > __fmul_rn(r.tol, dp)) ok = false;
-    }
-    wrs::Src src;
-    src.W = prev.W;
-    src.P = prev.P;
-    src.key = prev.key;
-    src.idx = prev.idx;
-    src.wt = prev.wt;
-    src.col = prev.col;
-    src.stride = prev.plane;
-    src.at = q;
-    src.frame = nullptr;
-    src.u = nullptr;
-    const int pi = static_cast<int>(p);
-    if constexpr (LIT)
-      replaced += wrs::push_group_literal<F16, 1, false, FOV, true>(cur, f, pi, src, d_f, !ok);
+    if constexpr (KT == 0)
+      replaced += reproject_literal<F16, FOV>(cur, prev, f, r, p, d_f);
     else
-      replaced += wrs::push_group<0, F16, 1, false, FOV, true>(cur, f, pi, src, d_f, !ok);
+      replaced += reproject_keys<KT, F16, FOV>(cur, prev, f, r, p, d_f);
   }
   const unsigned c = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(replaced));
   if ((threadIdx.x & 31) == 0 && c != 0) atomicAdd(&block_replaced, c);
@@ -82,13 +275,22 @@ __global__ void __launch_bounds__(kThreads) reproject_kernel(const __grid_consta
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-template <bool F16, bool LIT>
+template <int KT, bool F16>
 void launch(bool fov, unsigned grid, cudaStream_t st, const StreamDev& cur, const StreamDev& prev,
             const FrameDev& f, const ReprojDev& r) {
   if (fov)
-    reproject_kernel<F16, LIT, true><<<grid, kThreads, 0, st>>>(cur, prev, f, r);
+    reproject_kernel<KT, F16, true><<<grid, kThreads, 0, st>>>(cur, prev, f, r);
   else
-    reproject_kernel<F16, LIT, false><<<grid, kThreads, 0, st>>>(cur, prev, f, r);
+    reproject_kernel<KT, F16, false><<<grid, kThreads, 0, st>>>(cur, prev, f, r);
+}
+
+template <bool F16>
+void launch_k(int K, bool lit, bool fov, unsigned grid, cudaStream_t st, const StreamDev& cur,
+              const StreamDev& prev, const FrameDev& f, const ReprojDev& r) {
+  if (lit) launch<0, F16>(fov, grid, st, cur, prev, f, r);
+  else if (K <= 4) launch<4, F16>(fov, grid, st, cur, prev, f, r);
+  else if (K <= 8) launch<8, F16>(fov, grid, st, cur, prev, f, r);
+  else launch<16, F16>(fov, grid, st, cur, prev, f, r);
 }
 
 }  // namespace
@@ -187,13 +389,10 @@ extern "C" int wrs_push_frame_reproject(wrs_ctx* x, const float* d_frame, int64_
   const bool f16 = x->cfg.color_fp16 != 0;
   const bool lit = x->cfg.update_rule == WRS_RULE_LITERAL;
   const bool fov = d_fov != nullptr;
-  if (f16) {
-    if (lit) launch<true, true>(fov, grid, st, cur, prev, f, r);
-    else launch<true, false>(fov, grid, st, cur, prev, f, r);
-  } else {
-    if (lit) launch<false, true>(fov, grid, st, cur, prev, f, r);
-    else launch<false, false>(fov, grid, st, cur, prev, f, r);
-  }
+  if (f16)
+    launch_k<true>(x->cfg.K, lit, fov, grid, st, cur, prev, f, r);
+  else
+    launch_k<false>(x->cfg.K, lit, fov, grid, st, cur, prev, f, r);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_frame_reproject: launch");
   x->planes = dst_planes;

@@ -153,6 +153,23 @@ class Stream:
                 float(depth_tol), _dev_ptr(fov_map, torch.uint8, "fov_map"),
                 _dev_ptr(out, torch.float32, "out"), _stream_handle(stream)))
 
+    def push_foveated(self, foveation: "Foveation", gaze, fov_map: torch.Tensor | None = None,
+                      out: torch.Tensor | None = None, stream=None):
+        """Foveate this frame from ``foveation`` (image + mip buffer on the GPU)
+        and push it in one pass: the same reservoirs and output as
+        foveation.frame(gaze) followed by push_frame, without the frame in memory."""
+        fv = foveation
+        if (fv.height, fv.width) != (self.height, self.width):
+            raise ValueError("the foveation source must match the stream's size")
+        r = (C.c_float * len(fv.radii))(*fv.radii)
+        iptr, ipitch = _image_args(fv.img, "img")
+        with torch.cuda.device(self.device):
+            check(load().wrs_push_foveated(
+                self._ctx, iptr, ipitch, _dev_ptr(fv.mip, torch.uint8, "mip"), fv.mip.numel(),
+                len(fv.radii), r, FILTERS[fv.filter] if isinstance(fv.filter, str) else int(fv.filter),
+                float(gaze[0]), float(gaze[1]), _dev_ptr(fov_map, torch.uint8, "fov_map"),
+                _dev_ptr(out, torch.float32, "out"), _stream_handle(stream)))
+
     @property
     def frame_index(self) -> int:
         return int(load().wrs_frame_index(self._ctx))

@@ -176,3 +176,67 @@ def test_foveate_argument_errors():
         wrs.foveate(dimg, mip, (2.0,), (float("nan"), 4.0))
     with pytest.raises(wrs.WrsError, match="buffer holds"):
         wrs.mip_build(dimg, 4, out=torch.empty(256, dtype=torch.uint8, device="cuda"))
+
+
+@pytest.mark.parametrize("name", ["box", "bilinear"])
+@pytest.mark.parametrize("opts", [
+    {"K": 8}, {"K": 4}, {"K": 3}, {"K": 8, "color_fp16": True}, {"K": 1, "update_rule": 1},
+    {"K": 4, "temporal_bias": 2},
+])
+def test_push_foveated_equals_foveate_then_push(name, opts):
+    # foveating on read gives the reservoirs and output of wrs_foveate followed
+    # by wrs_push_frame, bit for bit, and both match the oracle
+    w, h = 160, 72
+    radii = (10.0, 25.0, 45.0)
+    opts = dict(opts)
+    K = opts.pop("K")
+    img, dimg = _image(w, h, seed=21)
+    fov = wrs.Foveation(dimg, radii, filter=name)
+    a = wrs.Stream(w, h, K, radii[0], seed=3, **opts)
+    b = wrs.Stream(w, h, K, radii[0], seed=3, **opts)
+    ost = oracle.OracleStream(w, h, K, radii[0], seed=3, rule=opts.get("update_rule", 0),
+                              temporal_bias=opts.get("temporal_bias", True),
+                              color_fp16=opts.get("color_fp16", False))
+    oa = torch.empty((h, w, 3), device="cuda")
+    ob = torch.empty((h, w, 3), device="cuda")
+    rng = np.random.default_rng(8)
+    f_id = oracle.FILTER_BOX if name == "box" else oracle.FILTER_BILINEAR
+    for t in range(9):
+        gaze = (float(rng.uniform(-10, w + 10)), float(rng.uniform(0, h)))
+        flush = None
+        if t == 6:
+            flush = torch.zeros((h, w), dtype=torch.uint8, device="cuda")
+            flush[10:30, 40:100] = 0xFF
+        a.push_foveated(fov, gaze, flush, oa)
+        frame, _ = fov.frame(gaze)
+        b.push_frame(frame, gaze, flush, ob)
+        ref, _ = oracle.foveate(img, radii, gaze[0], gaze[1], f_id)
+        ost.push_frame(ref, gaze, None if flush is None else flush.cpu().numpy())
+    torch.cuda.synchronize()
+    assert np.array_equal(a.export_raw(), b.export_raw())
+    assert torch.equal(oa.view(torch.int32), ob.view(torch.int32))
+    o = ost.state()
+    compare_states(a.export_state(), o, None, opts.get("color_fp16", False))
+    check_resolve(oa.cpu().numpy(), ost, o, opts.get("color_fp16", False))
+
+
+def test_push_foveated_4k_and_errors():
+    s = workload("4k").streams[0]
+    img, dimg = _image(s.width, s.height, seed=s.seed)
+    fov = wrs.Foveation(dimg, s.radii, filter="bilinear")
+    a = wrs.Stream(s.width, s.height, s.K, s.r_f, seed=1)
+    b = wrs.Stream(s.width, s.height, s.K, s.r_f, seed=1)
+    out_a = torch.empty((s.height, s.width, 3), device="cuda")
+    out_b = torch.empty_like(out_a)
+    for gaze in ((1920.0, 1080.0), (400.5, 1999.25), (3000.0, 20.0)):
+        a.push_foveated(fov, gaze, None, out_a)
+        frame, _ = fov.frame(gaze)
+        b.push_frame(frame, gaze, None, out_b)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.export_raw(), b.export_raw())
+    assert torch.equal(out_a.view(torch.int32), out_b.view(torch.int32))
+    odd = wrs.Stream(70, 8, 4, 3.0)
+    _, dodd = _image(70, 8, seed=0)
+    with pytest.raises(wrs.WrsError, match="width"):
+        odd.push_foveated(wrs.Foveation(dodd, (3.0,)), (5.0, 4.0))
+    assert odd.frame_index == 0
