@@ -6,9 +6,10 @@
 // cannot run in place: it reads one state buffer and writes every slot to the
 // other, and the buffers swap roles afterwards.
 //
-// One pixel per thread, its whole history held in registers: under a pan the
-// gathered rows are the current rows shifted, so neighbouring threads still
-// read neighbouring addresses.
+// One pixel per thread, its whole history gathered into the thread's column of
+// shared memory by asynchronous copies (the key race) or into registers (the
+// literal rule, one slot): under a pan the gathered rows are the current rows
+// shifted, so neighbouring threads still read neighbouring addresses.
 #include <cmath>
 
 #include "wrs_internal.h"
@@ -51,63 +52,119 @@ __device__ __forceinline__ int64_t source_pixel(const StreamDev& s, const Reproj
   return q;
 }
 
-// The key race for one pixel with its history gathered into registers: every
-// load of the pixel (frame, motion, depths, then the whole source reservoir)
-// is issued before any of it is used, and the arithmetic is the in-place
-// update's, step for step (push_group): Eq. (full-temporal-bias) factor from
-// the history's resolved colour, Eq. (temporal-bias), the key race, the fused
-// resolve, then every slot written to the other buffer. KT >= K bounds the
-// register arrays.
+// Asynchronous 4/8/16-byte global -> shared copies (no register holds the
+// data in flight), completed by cp.async.wait_all.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Shared staging of one block's gathered histories, one column per thread:
+// W, P, key[KT], idx[KT], then (FP32 colour) KT float4 records {w, r, g, b}
+// or (FP16 colour) KT weights and KT 8-byte half records.
+template <int KT, bool F16>
+struct Hist {
+  static constexpr int kW = 0;
+  static constexpr int kP = kW + 4 * kThreads;
+  static constexpr int kKey = kP + 4 * kThreads;
+  static constexpr int kIdx = kKey + 4 * KT * kThreads;
+  static constexpr int kWt = kIdx + 4 * KT * kThreads;               // FP16 only
+  static constexpr int kRec = F16 ? kWt + 4 * KT * kThreads : kWt;   // 16-byte aligned
+  static constexpr int kBytes = kRec + (F16 ? 8 : 16) * KT * kThreads;
+};
+
+// The key race for one pixel whose history the thread gathers into its
+// column of shared memory with asynchronous copies: the copies of the whole
+// source reservoir are issued at once, the uniform, weight and key are
+// computed while they fly, and the update then reads the history from shared
+// memory. The arithmetic is the in-place update's, step for step
+// (push_group): Eq. (full-temporal-bias) factor from the history's resolved
+// colour, Eq. (temporal-bias), the key race, the fused resolve, then every
+// slot written to the other buffer. KT >= K bounds the staging.
 template <int KT, bool F16, bool FOV>
 __device__ __forceinline__ int reproject_keys(const StreamDev& cur, const StreamDev& prev,
                                               const FrameDev& f, const ReprojDev& r, int64_t p,
-                                              float d_f) {
+                                              float d_f, uint8_t* smem) {
   using namespace wrs;
+  using H = Hist<KT, F16>;
   const int K = cur.K;
   const int64_t pl = cur.plane;
+  const int tid = threadIdx.x;
+  float* sW = reinterpret_cast<float*>(smem + H::kW) + tid;
+  float* sP = reinterpret_cast<float*>(smem + H::kP) + tid;
+  float* sKey = reinterpret_cast<float*>(smem + H::kKey) + tid;
+  uint32_t* sIdx = reinterpret_cast<uint32_t*>(smem + H::kIdx) + tid;
+  float* sWt = reinterpret_cast<float*>(smem + H::kWt) + tid;
+  uint8_t* sRec = smem + H::kRec + (F16 ? 8 : 16) * tid;
+  constexpr int kRecStride = (F16 ? 8 : 16) * kThreads;
+
   int y, x;
   row_col(cur, static_cast<int>(p), y, x);
+  const float dp = r.depth != nullptr ? r.depth[p] : 0.0f;
+  bool ok;
+  const int64_t q = source_pixel(cur, r, p, x, y, dp, ok);
+  cp_async4(sW, prev.W + q);
+  cp_async4(sP, prev.P + q);
+  for (int j = 0; j < K; ++j) {
+    cp_async4(sKey + j * kThreads, prev.key + j * pl + q);
+    cp_async4(sIdx + j * kThreads, prev.idx + j * pl + q);
+    if constexpr (F16) {
+      cp_async4(sWt + j * kThreads, prev.wt + j * pl + q);
+      cp_async8(sRec + j * kRecStride, static_cast<const uint2*>(prev.col) + j * pl + q);
+    } else {
+      cp_async16(sRec + j * kRecStride, static_cast<const float4*>(prev.col) + j * pl + q);
+    }
+  }
+
   const float* fp = f.frame + static_cast<int64_t>(y) * f.pitch + 3 * x;
   float rgb[3] = {fp[0], fp[1], fp[2]};
-  const float dp = r.depth != nullptr ? r.depth[p] : 0.0f;
-  bool flush = FOV && f.fov[p] == 0xFFu;
-
+  bool flush = (FOV && f.fov[p] == 0xFFu) || !ok;
   const uint4 blk = philox4x32_10(make_uint4(static_cast<uint32_t>(p) >> 2, f.t, cur.stream_id, 0u),
                                   cur.seed_lo, cur.seed_hi);
   const float u = unit_uniform(word(blk, static_cast<int>(p) & 3));
   const float w = pixel_weight(cur, d_f, x, y, f.gx, f.gy);
   const float k = fdiv(-log_pos(u), w);
+  cp_async_wait_all();
 
-  bool ok;
-  const int64_t q = source_pixel(cur, r, p, x, y, dp, ok);
-  float W = prev.W[q], P = prev.P[q];
-  float key[KT], a[KT], cr[KT], cg[KT], cb[KT];
-  uint32_t id[KT];
-#pragma unroll
-  for (int j = 0; j < KT; ++j) {
-    if (j < K) {
-      key[j] = prev.key[j * pl + q];
-      id[j] = prev.idx[j * pl + q];
-      float a1[1], r1[1], g1[1], b1[1];
-      load_slot<F16, 1>(prev.wt, prev.col, K, j, pl, q, a1, r1, g1, b1);
-      a[j] = a1[0]; cr[j] = r1[0]; cg[j] = g1[0]; cb[j] = b1[0];
+  // slot j of the gathered history, from this thread's column
+  auto slot = [&](int j, float& a, float& cr, float& cg, float& cb) {
+    if constexpr (F16) {
+      a = sWt[j * kThreads];
+      const uint2 v = *reinterpret_cast<const uint2*>(sRec + j * kRecStride);
+      cr = __half2float(__ushort_as_half(static_cast<unsigned short>(v.x & 0xffffu)));
+      cg = __half2float(__ushort_as_half(static_cast<unsigned short>(v.x >> 16)));
+      cb = __half2float(__ushort_as_half(static_cast<unsigned short>(v.y & 0xffffu)));
     } else {
-      key[j] = kInf; id[j] = kEmpty; a[j] = cr[j] = cg[j] = cb[j] = 0.0f;
+      const float4 v = *reinterpret_cast<const float4*>(sRec + j * kRecStride);
+      a = v.x; cr = v.y; cg = v.z; cb = v.w;
     }
-  }
-  flush = flush || !ok;
+  };
 
+  float W = *sW, P = *sP;
   float gl = 1.0f;
   if (cur.bias == 2) {
     float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f, dn = 0.0f;
-#pragma unroll
-    for (int j = 0; j < KT; ++j) {
-      if (j < K) {
-        n0 = __fmaf_rn(a[j], cr[j], n0);
-        n1 = __fmaf_rn(a[j], cg[j], n1);
-        n2 = __fmaf_rn(a[j], cb[j], n2);
-        dn = fadd(dn, a[j]);
-      }
+    for (int j = 0; j < K; ++j) {
+      float a, cr, cg, cb;
+      slot(j, a, cr, cg, cb);
+      n0 = __fmaf_rn(a, cr, n0);
+      n1 = __fmaf_rn(a, cg, n1);
+      n2 = __fmaf_rn(a, cb, n2);
+      dn = fadd(dn, a);
     }
     if (!flush && W > 0.0f) {
       gl = lightness_factor(n0, n1, n2, dn, rgb);
@@ -120,12 +177,9 @@ __device__ __forceinline__ int reproject_keys(const StreamDev& cur, const Stream
 
   float kmax = -1.0f;
   int jm = 0;
-#pragma unroll
-  for (int j = 0; j < KT; ++j) {
-    if (j < K) {
-      const float kj = race_key(key[j], flush, rescale);
-      if (kj > kmax) { kmax = kj; jm = j; }
-    }
+  for (int j = 0; j < K; ++j) {
+    const float kj = race_key(sKey[j * kThreads], flush, rescale);
+    if (kj > kmax) { kmax = kj; jm = j; }
   }
   const bool repl = ks < kmax;
   const float c0 = stored_colour<F16>(rgb[0]), c1 = stored_colour<F16>(rgb[1]),
@@ -133,17 +187,15 @@ __device__ __forceinline__ int reproject_keys(const StreamDev& cur, const Stream
 
   if (f.out != nullptr) {
     float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f, dn = 0.0f;
-#pragma unroll
-    for (int j = 0; j < KT; ++j) {
-      if (j < K) {
-        float aa = a[j], rr = cr[j], gg = cg[j], bb = cb[j];
-        if (flush) { aa = 0.0f; rr = gg = bb = 0.0f; }
-        if (repl && jm == j) { aa = w; rr = c0; gg = c1; bb = c2; }
-        n0 = __fmaf_rn(aa, rr, n0);
-        n1 = __fmaf_rn(aa, gg, n1);
-        n2 = __fmaf_rn(aa, bb, n2);
-        dn = fadd(dn, aa);
-      }
+    for (int j = 0; j < K; ++j) {
+      float aa, rr, gg, bb;
+      slot(j, aa, rr, gg, bb);
+      if (flush) { aa = 0.0f; rr = gg = bb = 0.0f; }
+      if (repl && jm == j) { aa = w; rr = c0; gg = c1; bb = c2; }
+      n0 = __fmaf_rn(aa, rr, n0);
+      n1 = __fmaf_rn(aa, gg, n1);
+      n2 = __fmaf_rn(aa, bb, n2);
+      dn = fadd(dn, aa);
     }
     const float inv = dn > 0.0f ? __frcp_rn(dn) : 0.0f;
     float* o = f.out + p * 3;
@@ -154,9 +206,7 @@ __device__ __forceinline__ int reproject_keys(const StreamDev& cur, const Stream
 
   cur.W[p] = W;
   cur.P[p] = P;
-#pragma unroll
-  for (int j = 0; j < KT; ++j) {
-    if (j >= K) continue;
+  for (int j = 0; j < K; ++j) {
     if (repl && j == jm) {
       cur.key[j * pl + p] = ks;
       cur.idx[j * pl + p] = f.t;
@@ -166,11 +216,19 @@ __device__ __forceinline__ int reproject_keys(const StreamDev& cur, const Stream
       cur.idx[j * pl + p] = kEmpty;
       store_slot<F16>(cur.wt, cur.col, K, j, pl, p, 0.0f, 0.0f, 0.0f, 0.0f);
     } else {
-      float kj = key[j];
+      float kj = sKey[j * kThreads];
       if (rescale && kj != kInf) kj = fminf(fmul(kj, kPScale), kFltMax);
       cur.key[j * pl + p] = kj;
-      cur.idx[j * pl + p] = id[j];
-      store_slot<F16>(cur.wt, cur.col, K, j, pl, p, a[j], cr[j], cg[j], cb[j]);
+      cur.idx[j * pl + p] = sIdx[j * kThreads];
+      if constexpr (F16) {
+        // the half record moves unchanged; its weight beside it
+        cur.wt[j * pl + p] = sWt[j * kThreads];
+        static_cast<uint2*>(cur.col)[j * pl + p] =
+            *reinterpret_cast<const uint2*>(sRec + j * kRecStride);
+      } else {
+        static_cast<float4*>(cur.col)[j * pl + p] =
+            *reinterpret_cast<const float4*>(sRec + j * kRecStride);
+      }
     }
   }
   return repl ? 1 : 0;
@@ -248,12 +306,14 @@ __device__ __forceinline__ int reproject_literal(const StreamDev& cur, const Str
   return take ? 1 : 0;
 }
 
-// KT > 0: the key race with K <= KT slots; KT == 0: the literal rule.
+// KT > 0: the key race with K <= KT slots, histories staged in dynamic
+// shared memory (Hist<KT, F16>::kBytes); KT == 0: the literal rule.
 template <int KT, bool F16, bool FOV>
 __global__ void __launch_bounds__(kThreads) reproject_kernel(const __grid_constant__ StreamDev cur,
                                                              const __grid_constant__ StreamDev prev,
                                                              const __grid_constant__ FrameDev f,
                                                              const __grid_constant__ ReprojDev r) {
+  extern __shared__ __align__(16) uint8_t hist_smem[];
   __shared__ unsigned block_replaced;
   if (threadIdx.x == 0) block_replaced = 0;
   __syncthreads();
@@ -264,7 +324,7 @@ __global__ void __launch_bounds__(kThreads) reproject_kernel(const __grid_consta
     if constexpr (KT == 0)
       replaced += reproject_literal<F16, FOV>(cur, prev, f, r, p, d_f);
     else
-      replaced += reproject_keys<KT, F16, FOV>(cur, prev, f, r, p, d_f);
+      replaced += reproject_keys<KT, F16, FOV>(cur, prev, f, r, p, d_f, hist_smem);
   }
   const unsigned c = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(replaced));
   if ((threadIdx.x & 31) == 0 && c != 0) atomicAdd(&block_replaced, c);
@@ -275,22 +335,43 @@ __global__ void __launch_bounds__(kThreads) reproject_kernel(const __grid_consta
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+template <int KT, bool F16, bool FOV>
+cudaError_t launch_fov(unsigned grid, cudaStream_t st, const StreamDev& cur, const StreamDev& prev,
+                       const FrameDev& f, const ReprojDev& r) {
+  const size_t smem = KT > 0 ? Hist<(KT > 0 ? KT : 1), F16>::kBytes : 0;
+  if (smem > 48 * 1024) {
+    // per instantiation and device: allow the staging once
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!configured[dev]) {
+      e = cudaFuncSetAttribute(reproject_kernel<KT, F16, FOV>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+      if (e != cudaSuccess) return e;
+      configured[dev] = true;
+    }
+  }
+  reproject_kernel<KT, F16, FOV><<<grid, kThreads, smem, st>>>(cur, prev, f, r);
+  return cudaGetLastError();
+}
+
 template <int KT, bool F16>
-void launch(bool fov, unsigned grid, cudaStream_t st, const StreamDev& cur, const StreamDev& prev,
-            const FrameDev& f, const ReprojDev& r) {
-  if (fov)
-    reproject_kernel<KT, F16, true><<<grid, kThreads, 0, st>>>(cur, prev, f, r);
-  else
-    reproject_kernel<KT, F16, false><<<grid, kThreads, 0, st>>>(cur, prev, f, r);
+cudaError_t launch(bool fov, unsigned grid, cudaStream_t st, const StreamDev& cur,
+                   const StreamDev& prev, const FrameDev& f, const ReprojDev& r) {
+  return fov ? launch_fov<KT, F16, true>(grid, st, cur, prev, f, r)
+             : launch_fov<KT, F16, false>(grid, st, cur, prev, f, r);
 }
 
 template <bool F16>
-void launch_k(int K, bool lit, bool fov, unsigned grid, cudaStream_t st, const StreamDev& cur,
-              const StreamDev& prev, const FrameDev& f, const ReprojDev& r) {
-  if (lit) launch<0, F16>(fov, grid, st, cur, prev, f, r);
-  else if (K <= 4) launch<4, F16>(fov, grid, st, cur, prev, f, r);
-  else if (K <= 8) launch<8, F16>(fov, grid, st, cur, prev, f, r);
-  else launch<16, F16>(fov, grid, st, cur, prev, f, r);
+cudaError_t launch_k(int K, bool lit, bool fov, unsigned grid, cudaStream_t st,
+                     const StreamDev& cur, const StreamDev& prev, const FrameDev& f,
+                     const ReprojDev& r) {
+  if (lit) return launch<0, F16>(fov, grid, st, cur, prev, f, r);
+  if (K <= 4) return launch<4, F16>(fov, grid, st, cur, prev, f, r);
+  if (K <= 8) return launch<8, F16>(fov, grid, st, cur, prev, f, r);
+  return launch<16, F16>(fov, grid, st, cur, prev, f, r);
 }
 
 }  // namespace
@@ -389,11 +470,8 @@ extern "C" int wrs_push_frame_reproject(wrs_ctx* x, const float* d_frame, int64_
   const bool f16 = x->cfg.color_fp16 != 0;
   const bool lit = x->cfg.update_rule == WRS_RULE_LITERAL;
   const bool fov = d_fov != nullptr;
-  if (f16)
-    launch_k<true>(x->cfg.K, lit, fov, grid, st, cur, prev, f, r);
-  else
-    launch_k<false>(x->cfg.K, lit, fov, grid, st, cur, prev, f, r);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = f16 ? launch_k<true>(x->cfg.K, lit, fov, grid, st, cur, prev, f, r)
+                      : launch_k<false>(x->cfg.K, lit, fov, grid, st, cur, prev, f, r);
   if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_frame_reproject: launch");
   x->planes = dst_planes;
   x->t += 1;
