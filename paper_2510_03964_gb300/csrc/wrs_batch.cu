@@ -38,6 +38,12 @@ struct BatchEntry {
                // 5 any K f32, 6 literal f16, 7 literal f32
 };
 
+// The slot records are staged when the fused resolve needs them or the full
+// temporal bias forms the history's resolved colour from them.
+__device__ __forceinline__ bool stage_records(const BatchEntry& e) {
+  return e.f.out != nullptr || e.s.bias == 2;
+}
+
 struct BatchArgs {
   int n;
   int ntiles;
@@ -91,7 +97,7 @@ __global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
                             const BatchEntry& e = a.e[entry_of(a, g)];
                             const int64_t p0 = static_cast<int64_t>(g - e.tile0) * T;
                             const int cs = entry_f16(e) ? 2 : 4;
-                            const bool resolve = e.f.out != nullptr;
+                            const bool resolve = stage_records(e);
                             const StageLayout L = wrs::stage_layout(T, e.s.K, cs, resolve);
                             wrs::draw_tile_uniforms_warp<T>(e.s, e.f, p0, u, ln);
                             __syncwarp();
@@ -103,7 +109,7 @@ __global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
       const int g = first + it * step;
       const BatchEntry& e = a.e[entry_of(a, g)];
       const int64_t p0 = static_cast<int64_t>(g - e.tile0) * T;
-      const bool resolve = e.f.out != nullptr;
+      const bool resolve = stage_records(e);
       const float d_f = wrs::fovea_density(e.s);
       int rc;
       switch (e.code) {
@@ -271,7 +277,8 @@ extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
     e.tile0 = static_cast<int>(tiles);
     e.code = code_of(x->cfg);
     tiles += (static_cast<int64_t>(e.s.hw) + T - 1) / T;
-    const uint32_t sb = wrs::stage_layout(T, x->cfg.K, x->cfg.color_fp16 ? 2 : 4, out != nullptr).bytes;
+    const bool records = out != nullptr || x->cfg.temporal_bias == 2;
+    const uint32_t sb = wrs::stage_layout(T, x->cfg.K, x->cfg.color_fp16 ? 2 : 4, records).bytes;
     if (sb > stage_bytes) stage_bytes = sb;
   }
   if (tiles > 0x7FFFFFFF) return wrs_fail(WRS_ERR_ARG, "batch too large");

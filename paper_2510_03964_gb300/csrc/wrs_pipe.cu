@@ -33,7 +33,7 @@ namespace {
 struct PipeArgs {
   int stages;
   int ntiles;
-  int resolve;             // copy weight/colour planes (f.out != null)
+  int resolve;             // copy weight/colour planes (fused resolve or full temporal bias)
   uint32_t* status;        // stream status word (WRS_OK or WRS_ERR_TIMEOUT)
   uint64_t timeout_ns;
   uint32_t extra_tx;       // added to the expected bytes: > 0 only to test the timeout path
@@ -184,7 +184,7 @@ cudaError_t wrs_launch_pipe_fov(const StreamDev& s, const FrameDev& f, const Fov
   PipeArgs a;
   a.stages = stages;
   a.ntiles = 0;
-  a.resolve = f.out != nullptr ? 1 : 0;
+  a.resolve = (f.out != nullptr || s.bias == 2) ? 1 : 0;  // records: resolve or Delta L
   a.status = status;
   a.timeout_ns = timeout_ns;
   a.extra_tx = 0;
@@ -201,7 +201,7 @@ cudaError_t wrs_launch_pipe(const StreamDev& s, const FrameDev& f, bool f16, int
   PipeArgs a;
   a.stages = stages;
   a.ntiles = 0;
-  a.resolve = f.out != nullptr ? 1 : 0;
+  a.resolve = (f.out != nullptr || s.bias == 2) ? 1 : 0;  // records: resolve or Delta L
   a.status = status;
   a.timeout_ns = timeout_ns;
   a.extra_tx = extra_tx;

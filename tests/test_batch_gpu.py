@@ -159,3 +159,29 @@ def test_batch_mixes_literal_and_key_streams():
         orc.push_frame(data[0][t][0].cpu().numpy(), data[0][t][1])
     compare_states(mixed[0].export_state(), orc.state(), None, False)
     b.close()
+
+
+def test_batch_full_temporal_bias_without_outputs():
+    # Eq. (full-temporal-bias) reads the slots' colours even when no output is
+    # written: batched pushes without outputs equal solo pushes and the oracle
+    dev = torch.device("cuda")
+    specs = MIX[:4]
+    frames = 6
+    data = _frames(specs, frames, seed0=30)
+    solo = [wrs.Stream(w, h, K, rf, seed=30 + i, stream_id=i, color_fp16=f16, device=dev,
+                       temporal_bias=2) for i, (w, h, K, f16, rf) in enumerate(specs)]
+    mixed = [wrs.Stream(w, h, K, rf, seed=30 + i, stream_id=i, color_fp16=f16, device=dev,
+                        temporal_bias=2) for i, (w, h, K, f16, rf) in enumerate(specs)]
+    orc = oracle.OracleStream(*specs[0][:3], specs[0][4], seed=30, stream_id=0, temporal_bias=2,
+                              color_fp16=specs[0][3])
+    b = wrs.Batch(8)
+    for t in range(frames):
+        for i, s in enumerate(solo):
+            s.push_frame(data[i][t][0], data[i][t][1])
+        b.push(mixed, [data[i][t][0] for i in range(len(specs))], [data[i][t][1] for i in range(len(specs))])
+        orc.push_frame(data[0][t][0].cpu().numpy(), data[0][t][1])
+    torch.cuda.synchronize()
+    for i in range(len(specs)):
+        assert_bits_equal(mixed[i].export_raw(), solo[i].export_raw(), f"stream {i} state")
+    compare_states(mixed[0].export_state(), orc.state(), None, specs[0][3])
+    b.close()

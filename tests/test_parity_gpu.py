@@ -314,6 +314,20 @@ def test_full_temporal_bias_bit_exact(K, rule, fp16, pipeline):
             run.compare()
 
 
+@pytest.mark.parametrize("K,rule,fp16,pipeline", [
+    (4, 0, False, (True, 0, 0, 0)), (8, 0, True, (True, 2, 2, 0)), (1, 1, False, (True, 0, 0, 0)),
+    (3, 0, False, (False, 0, 0, 0))])
+def test_full_temporal_bias_without_fused_resolve(K, rule, fp16, pipeline):
+    """Eq. (full-temporal-bias) needs the slots' colours even when no output
+    is written: pushes without `out` must give the same planes."""
+    run = PairedRun(96, 40, K, r_f=10.0, frames=10, seed=43, jitter_px=20, color_fp16=fp16,
+                    pipeline=pipeline, update_rule=rule, temporal_bias=2, switch_scene_at=5)
+    for t in range(10):
+        run.step(t, fused=False)
+    torch.cuda.synchronize()
+    run.compare(check_out=False)
+
+
 def test_full_temporal_bias_4k_sampled():
     s = workload("4k").streams[0]
     pix = _sample_pixels(s.width, s.height, 8192, 4)
