@@ -158,6 +158,43 @@ int wrs_push_frame_host(wrs_ctx* ctx, const float* h_frame, float gaze_x, float 
                         const uint8_t* h_fov_map, float* h_out, float* d_frame_stage,
                         uint8_t* d_fov_stage, float* d_out_stage, wrs_stream_t stream);
 
+/* Pipelined host-buffer frames: the upload of frame n, the update of frame
+ * n-1 and the download of frame n-2's resolved output overlap on three CUDA
+ * streams the pipeline owns, through two device staging slots for frames and
+ * outputs (and fov maps) in a caller-owned buffer. Each frame gets the same
+ * update and output as wrs_push_frame_host. Not a step of the paper's method:
+ * it moves frames between host memory and the device. */
+typedef struct wrs_host_pipe wrs_host_pipe;
+
+/* Device staging bytes the pipeline needs: two frames and two outputs of
+ * width * height RGB floats (and two width * height fov maps if with_fov),
+ * each 256-byte aligned. 0 for a NULL context. */
+size_t wrs_host_pipe_stage_bytes(const wrs_ctx* ctx, int with_fov);
+
+/* Creates a pipeline for `ctx` on d_stage (caller-owned, 256-byte aligned,
+ * at least wrs_host_pipe_stage_bytes bytes, on the context's device, which
+ * must be current). The pipeline owns its streams and events. Errors:
+ * WRS_ERR_ARG, WRS_ERR_BUDGET, WRS_ERR_CUDA. */
+int wrs_host_pipe_create(wrs_ctx* ctx, void* d_stage, size_t bytes, int with_fov,
+                         wrs_host_pipe** out);
+
+/* Enqueues one frame: h_frame [height][width][3] floats is uploaded
+ * asynchronously, the context's update and fused resolve run, and the
+ * resolved frame is downloaded to h_out asynchronously. Before enqueuing
+ * frame n the call waits until frame n-2 is complete, so at most two frames
+ * are in flight and the host buffers of frame n-2 and older are free again.
+ * h_frame, h_fov_map (nullable) and h_out of the last two frames must stay
+ * valid and unmodified until wrs_host_pipe_finish (pinned host memory makes
+ * the copies asynchronous). Errors: as wrs_push_frame, WRS_ERR_CUDA. */
+int wrs_host_pipe_push(wrs_host_pipe* p, const float* h_frame, float gaze_x, float gaze_y,
+                       const uint8_t* h_fov_map, float* h_out);
+
+/* Waits until every enqueued frame's output is in its host buffer. */
+int wrs_host_pipe_finish(wrs_host_pipe* p);
+
+/* Finishes, then releases the streams and events (not the stage buffer). */
+int wrs_host_pipe_destroy(wrs_host_pipe* p);
+
 /* Copies the whole state buffer to / from host memory (layout per
  * wrs_state_layout) and waits for the copy. Used for checkpoints, migration
  * of a stream between devices, and tests. Import also sets the frame counter. */

@@ -8,11 +8,11 @@ the library does all of the work, and nothing falls back to the CPU: without
 the built library every call raises.
 """
 from ._lib import WrsError, header_functions, load
-from .wrs import (Batch, Foveation, Stream, foveate, make_config, mip_build, mip_layout, mip_levels,
+from .wrs import (Batch, Foveation, HostPipeline, Stream, foveate, make_config, mip_build, mip_layout, mip_levels,
                   state_bytes, state_layout, unpack_state)
 
 __all__ = ["Batch", "Stream", "make_config", "state_bytes", "state_layout", "unpack_state", "WrsError",
-           "load", "header_functions", "Foveation", "foveate", "mip_build", "mip_layout", "mip_levels"]
+           "load", "header_functions", "Foveation", "HostPipeline", "foveate", "mip_build", "mip_layout", "mip_levels"]
 
 
 def kernel_source_hash() -> str:

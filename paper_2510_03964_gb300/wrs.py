@@ -311,6 +311,52 @@ class Batch:
             pass
 
 
+# ------------------------------------------------------------ pipelined host frames
+
+class HostPipeline:
+    """Frames in host memory through one stream with the upload of the next
+    frame, the update of this one and the download of the previous output
+    overlapping (wrs_host_pipe_*). Host tensors should be pinned; the last two
+    frames' buffers must stay untouched until finish()."""
+
+    def __init__(self, stream: Stream, with_fov: bool = False):
+        self.stream = stream
+        lib = load()
+        n = int(lib.wrs_host_pipe_stage_bytes(stream._ctx, 1 if with_fov else 0))
+        self.stage = torch.empty(n, dtype=torch.uint8, device=stream.device)
+        self._p = C.c_void_p()
+        with torch.cuda.device(stream.device):
+            check(lib.wrs_host_pipe_create(stream._ctx, self.stage.data_ptr(), n, 1 if with_fov else 0,
+                                           C.byref(self._p)))
+        self.hw = stream.width * stream.height
+
+    def push(self, h_frame: torch.Tensor, gaze, h_out: torch.Tensor, h_fov: torch.Tensor | None = None):
+        for t, n, name in ((h_frame, 3 * self.hw, "h_frame"), (h_out, 3 * self.hw, "h_out")):
+            if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != n:
+                raise ValueError(f"{name} must be a contiguous host float32 tensor of {n} values")
+        if h_fov is not None and (h_fov.is_cuda or h_fov.dtype != torch.uint8 or h_fov.numel() != self.hw):
+            raise ValueError("h_fov must be a host uint8 tensor of width * height values")
+        with torch.cuda.device(self.stream.device):
+            check(load().wrs_host_pipe_push(self._p, h_frame.data_ptr(), float(gaze[0]), float(gaze[1]),
+                                            None if h_fov is None else h_fov.data_ptr(), h_out.data_ptr()))
+
+    def finish(self):
+        with torch.cuda.device(self.stream.device):
+            check(load().wrs_host_pipe_finish(self._p))
+
+    def close(self):
+        if self._p:
+            with torch.cuda.device(self.stream.device):
+                load().wrs_host_pipe_destroy(self._p)
+            self._p = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ------------------------------------------------------------ foveation post-process
 
 FILTERS = {"box": WRS_FILTER_BOX, "bilinear": WRS_FILTER_BILINEAR}
