@@ -266,28 +266,32 @@ def run_batched(args, dev):
         return [wrs.Stream(s.width, s.height, s.K, s.r_f, seed=s.seed, stream_id=s.stream_id,
                            color_fp16=s.color_fp16, device=dev, stream=stream) for s in specs]
 
-    def timed(fn, rounds):
-        for r in range(3):
+    warm = max(3, args.batch_warmup)
+    counts = {}
+
+    def timed(fn, rounds, streams):
+        for r in range(warm):
             fn(r)
         torch.cuda.synchronize()
+        r0 = sum(x.replacements(stream=stream) for x in streams)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for r in range(rounds):
-            fn(3 + r)
+            fn(warm + r)
         b.record(stream)
         torch.cuda.synchronize()
+        counts["rho"] = (sum(x.replacements(stream=stream) for x in streams) - r0) / float(wl.pixels * rounds)
         return a.elapsed_time(b) / rounds
 
     sts = make()
     batch = wrs.Batch(len(specs))
     batch.set_launch(*tuned["batch"])
-    r0 = sum(x.replacements(stream=stream) for x in sts)
 
     def batched_round(t):
         batch.push(sts, [f[t % nfr] for f in frames], [g[t % nfr] for g in gazes], outs=outs, stream=stream)
 
-    ms_batch = timed(batched_round, args.batch_rounds)
-    rho = (sum(x.replacements(stream=stream) for x in sts) - r0) / float(wl.pixels * (args.batch_rounds + 3))
+    ms_batch = timed(batched_round, args.batch_rounds, sts)
+    rho = counts["rho"]
     for x in sts:
         x.close()
     sts2 = make()
@@ -296,7 +300,7 @@ def run_batched(args, dev):
         for i, x in enumerate(sts2):
             x.push_frame(frames[i][t % nfr], gazes[i][t % nfr], None, outs[i], stream=stream)
 
-    ms_solo = timed(solo_round, args.batch_rounds)
+    ms_solo = timed(solo_round, args.batch_rounds, sts2)
     for x in sts2:
         x.close()
     batch.close()
@@ -306,6 +310,7 @@ def run_batched(args, dev):
     achieved = bytes_round / (ms_batch * 1e-3) / 1e9
     del frames, outs
     return {"workload": wl.description, "pixels_per_round": wl.pixels, "rounds": args.batch_rounds,
+            "warmup_rounds": warm,
             "ms_per_round_batched": round(ms_batch, 4), "ms_per_round_16_launches": round(ms_solo, 4),
             "mpx_updates_per_s": round(wl.pixels / (ms_batch * 1e-3) / 1e6, 1),
             "replacement_rate": round(rho, 4),
@@ -764,7 +769,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=131072)
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--ref-sample", type=int, default=65536)
-    ap.add_argument("--batch-rounds", type=int, default=100,
+    ap.add_argument("--batch-warmup", type=int, default=100,
+                    help="untimed rounds before the timed ones (the streams' reservoirs fill first)")
+    ap.add_argument("--batch-rounds", type=int, default=200,
                     help="rounds of the 16-stream batched workload (0 skips it)")
     ap.add_argument("--fov-reps", type=int, default=50,
                     help="timed calls of each foveation kernel (0 skips the foveation section)")

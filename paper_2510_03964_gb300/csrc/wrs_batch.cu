@@ -71,13 +71,19 @@ __device__ __forceinline__ bool entry_f16(const BatchEntry& e) {
 constexpr int kConsumerWarps = 8;
 constexpr int kBatchThreads = (kConsumerWarps + 1) * 32;
 
+// Arithmetic families: a batch whose streams all use FP16 colour with K = 4
+// or 8 (the serving mix) or all FP32 colour with K = 4 or 8 gets a kernel
+// holding only those two variants; any other mix gets the kernel with all.
+constexpr int kFamF16K48 = 0, kFamF32K48 = 1, kFamAll = 2;
+
 // Warp-specialised like the single-stream pipelined kernel: warp 8 draws each
 // tile's uniforms and issues its copies, warps 0..7 compute it.
-template <int PX>
+template <int PX, int FAM>
 __global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
     batch_kernel(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ unsigned long long replaced_s[kMaxBatch];  // per stream, this CTA
+  __shared__ float d_f_s[kMaxBatch];                    // per stream: density at the fovea edge
   constexpr int T = kConsumerWarps * 32 * PX;
   const wrs::Ring r = wrs::make_ring(smem, a.stage_bytes, T, a.stages);
   const int tid = threadIdx.x;
@@ -85,6 +91,8 @@ __global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
   const int lane = tid & 31;
   if (tid == 0) wrs::init_ring(r, kConsumerWarps);
   if (tid < kMaxBatch) replaced_s[tid] = 0;
+  // each stream's Eq. (phat) normaliser, once per CTA instead of once per tile
+  if (tid < a.n) d_f_s[tid] = wrs::fovea_density(a.e[tid].s);
   __syncthreads();
 
   const int first = blockIdx.x, step = gridDim.x;
@@ -107,12 +115,22 @@ __global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
   } else {
     wrs::consume(r, my_tiles, a.timeout_ns, lane, [&](int it, const uint8_t* st, const float* u) {
       const int g = first + it * step;
-      const BatchEntry& e = a.e[entry_of(a, g)];
+      const int ei = entry_of(a, g);
+      const BatchEntry& e = a.e[ei];
       const int64_t p0 = static_cast<int64_t>(g - e.tile0) * T;
       const bool resolve = stage_records(e);
-      const float d_f = wrs::fovea_density(e.s);
+      const float d_f = d_f_s[ei];
       int rc;
-      switch (e.code) {
+      if constexpr (FAM == kFamF16K48) {
+        rc = e.code == 0
+                 ? wrs::compute_tile<4, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 2, resolve), st, u, p0, d_f, tid)
+                 : wrs::compute_tile<8, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 2, resolve), st, u, p0, d_f, tid);
+      } else if constexpr (FAM == kFamF32K48) {
+        rc = e.code == 2
+                 ? wrs::compute_tile<4, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 4, resolve), st, u, p0, d_f, tid)
+                 : wrs::compute_tile<8, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 4, resolve), st, u, p0, d_f, tid);
+      } else {
+        switch (e.code) {
         case 0: rc = wrs::compute_tile<4, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 2, resolve), st, u, p0, d_f, tid); break;
         case 1: rc = wrs::compute_tile<8, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 2, resolve), st, u, p0, d_f, tid); break;
         case 2: rc = wrs::compute_tile<4, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 4, resolve), st, u, p0, d_f, tid); break;
@@ -121,9 +139,10 @@ __global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
         case 6: rc = wrs::compute_tile<1, true, PX, T, true>(e.s, e.f, wrs::stage_layout(T, 1, 2, resolve), st, u, p0, d_f, tid); break;
         case 7: rc = wrs::compute_tile<1, false, PX, T, true>(e.s, e.f, wrs::stage_layout(T, 1, 4, resolve), st, u, p0, d_f, tid); break;
         default: rc = wrs::compute_tile<0, false, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 4, resolve), st, u, p0, d_f, tid); break;
+        }
       }
       const unsigned c = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(rc));
-      if (lane == 0 && c != 0) atomicAdd(&replaced_s[entry_of(a, g)], static_cast<unsigned long long>(c));
+      if (lane == 0 && c != 0) atomicAdd(&replaced_s[ei], static_cast<unsigned long long>(c));
     });
   }
   __syncthreads();
@@ -136,17 +155,23 @@ __global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
 }
 
 template <int PX>
-const void* batch_fn() {
-  return reinterpret_cast<const void*>(&batch_kernel<PX>);
-}
-
-const void* batch_kernel_for(int px) {
-  switch (px) {
-    case 4: return batch_fn<4>();
-    case 2: return batch_fn<2>();
-    default: return batch_fn<1>();
+const void* batch_fn(int fam) {
+  switch (fam) {
+    case kFamF16K48: return reinterpret_cast<const void*>(&batch_kernel<PX, kFamF16K48>);
+    case kFamF32K48: return reinterpret_cast<const void*>(&batch_kernel<PX, kFamF32K48>);
+    default: return reinterpret_cast<const void*>(&batch_kernel<PX, kFamAll>);
   }
 }
+
+const void* batch_kernel_for(int px, int fam) {
+  switch (px) {
+    case 4: return batch_fn<4>(fam);
+    case 2: return batch_fn<2>(fam);
+    default: return batch_fn<1>(fam);
+  }
+}
+
+constexpr int kSlots = 9;  // 3 pixels-per-thread choices x 3 families
 
 }  // namespace
 
@@ -154,16 +179,25 @@ struct wrs_batch {
   int max_streams;
   int px, stages, ctas_per_sm, use_graph;
   BatchArgs* args;            // host copy of the launch descriptor
-  // one captured graph per pixels-per-thread choice
-  cudaGraph_t graph[3];
-  cudaGraphExec_t exec[3];
-  cudaGraphNode_t node[3];
-  size_t configured_smem[3];
+  // one captured graph per pixels-per-thread choice and family
+  cudaGraph_t graph[kSlots];
+  cudaGraphExec_t exec[kSlots];
+  cudaGraphNode_t node[kSlots];
+  size_t configured_smem[kSlots];
   int device;
   int rebuilds;  // graph nodes rebuilt because an in-place update was refused
 };
 
 static int px_slot(int px) { return px == 4 ? 2 : (px == 2 ? 1 : 0); }
+
+static int family_of(const BatchArgs& a) {
+  bool f16 = true, f32 = true;
+  for (int i = 0; i < a.n; ++i) {
+    f16 = f16 && (a.e[i].code == 0 || a.e[i].code == 1);
+    f32 = f32 && (a.e[i].code == 2 || a.e[i].code == 3);
+  }
+  return f16 ? kFamF16K48 : (f32 ? kFamF32K48 : kFamAll);
+}
 
 extern "C" int wrs_batch_create(int max_streams, wrs_batch** out) {
   if (!out) return wrs_fail(WRS_ERR_ARG, "output pointer is NULL");
@@ -191,7 +225,7 @@ extern "C" int wrs_batch_create(int max_streams, wrs_batch** out) {
 
 extern "C" int wrs_batch_destroy(wrs_batch* b) {
   if (!b) return WRS_OK;
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < kSlots; ++i) {
     if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
     if (b->graph[i]) cudaGraphDestroy(b->graph[i]);
   }
@@ -284,7 +318,11 @@ extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
   if (tiles > 0x7FFFFFFF) return wrs_fail(WRS_ERR_ARG, "batch too large");
   int stages = b->stages;
   if (stages == 0) {
-    stages = 2;
+    // as many stages (up to 4) as keep two CTAs on an SM, else what one CTA holds
+    constexpr size_t kSmPerSm = 228 * 1024, kReservedPerCta = 1024;
+    stages = 4;
+    while (stages > 2 && 2 * (wrs::ring_bytes(stage_bytes, T, stages) + kReservedPerCta) > kSmPerSm)
+      --stages;
     while (stages > 1 && wrs::ring_bytes(stage_bytes, T, stages) > kSmemBudget) --stages;
   }
   const size_t smem = wrs::ring_bytes(stage_bytes, T, stages);
@@ -296,12 +334,13 @@ extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
   a.stage_bytes = stage_bytes;
   a.timeout_ns = ctxs[0]->timeout_ns;
 
-  const int slot = px_slot(b->px);
-  const void* fn = batch_kernel_for(b->px);
+  const int fam = family_of(a);
+  const int slot = px_slot(b->px) * 3 + fam;
+  const void* fn = batch_kernel_for(b->px, fam);
   cudaError_t e = cudaSuccess;
   if (b->device != device) {
     // a new device: drop graphs and attribute settings made for another one
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < kSlots; ++i) {
       if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
       if (b->graph[i]) cudaGraphDestroy(b->graph[i]);
       b->exec[i] = nullptr;
