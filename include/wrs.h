@@ -158,6 +158,26 @@ int wrs_push_frame_host(wrs_ctx* ctx, const float* h_frame, float gaze_x, float 
                         const uint8_t* h_fov_map, float* h_out, float* d_frame_stage,
                         uint8_t* d_fov_stage, float* d_out_stage, wrs_stream_t stream);
 
+/* Largest frame (pixels) wrs_push_frame_host_noalloc stages: 3840 x 2160. */
+#define WRS_NOALLOC_MAX_PIXELS 8294400
+
+/* wrs_push_frame_host for callers that cannot allocate device memory: the
+ * device copies of the frame, the fov map and the resolved output live in a
+ * file-scope device array of the library (2 * 12 + 1 bytes per pixel of
+ * WRS_NOALLOC_MAX_PIXELS, one copy per device), found with
+ * cudaGetSymbolAddress for the stream's device, which must be current. The
+ * caller still owns the reservoir state buffer. The paper has no counterpart:
+ * this only moves frames between host memory and the device. Arguments,
+ * results and errors as wrs_push_frame_host, plus WRS_ERR_ARG for frames
+ * above WRS_NOALLOC_MAX_PIXELS or another device being current. Allocates no
+ * memory. Calls that overlap (from several host threads, or on several CUDA
+ * streams of one device, for any stream) share the one staging array and race;
+ * serialise them. The first call on a device loads the library's device code
+ * and resolves the array's address: make it before any stream capture. The
+ * call waits for its copies, as wrs_push_frame_host does. */
+int wrs_push_frame_host_noalloc(wrs_ctx* ctx, const float* h_frame, float gaze_x, float gaze_y,
+                                const uint8_t* h_fov_map, float* h_out, wrs_stream_t stream);
+
 /* Pipelined host-buffer frames: the upload of frame n, the update of frame
  * n-1 and the download of frame n-2's resolved output overlap on three CUDA
  * streams the pipeline owns, through two device staging slots for frames and

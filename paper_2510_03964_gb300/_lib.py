@@ -74,6 +74,7 @@ SIGNATURES = {
                          C.c_float, C.c_float, C.c_int32, _V, C.c_int64, _V, _V]),
     "wrs_push_foveated": (_I, [_V, _V, C.c_int64, _V, C.c_size_t, C.c_int32, _V, C.c_int32, C.c_float,
                                C.c_float, _V, _V, _V]),
+    "wrs_push_frame_host_noalloc": (_I, [_V, _V, C.c_float, C.c_float, _V, _V, _V]),
     "wrs_host_pipe_stage_bytes": (C.c_size_t, [_V, _I]),
     "wrs_host_pipe_create": (_I, [_V, _V, C.c_size_t, _I, C.POINTER(_V)]),
     "wrs_host_pipe_push": (_I, [_V, _V, C.c_float, C.c_float, _V, _V]),

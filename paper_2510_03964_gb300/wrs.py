@@ -219,6 +219,19 @@ class Stream:
             _dev_ptr(d_fov_stage, torch.uint8, "d_fov_stage"),
             _dev_ptr(d_out_stage, torch.float32, "d_out_stage"), _stream_handle(stream)))
 
+    def push_frame_host_noalloc(self, h_frame: torch.Tensor, gaze, h_out: torch.Tensor,
+                                h_fov_map=None, stream=None):
+        """Host frame in, host resolved frame out, staged in the library's own
+        device array (wrs_push_frame_host_noalloc): no device buffers needed."""
+        for t, n in ((h_frame, "h_frame"), (h_out, "h_out")):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"{n} must be a contiguous host tensor")
+        with torch.cuda.device(self.device):
+            check(load().wrs_push_frame_host_noalloc(
+                self._ctx, h_frame.data_ptr(), float(gaze[0]), float(gaze[1]),
+                None if h_fov_map is None else h_fov_map.data_ptr(), h_out.data_ptr(),
+                _stream_handle(stream)))
+
     def export_raw(self, stream=None) -> np.ndarray:
         buf = np.empty(self.nbytes, dtype=np.uint8)
         check(load().wrs_export_state(self._ctx, buf.ctypes.data, buf.nbytes, _stream_handle(stream)))
