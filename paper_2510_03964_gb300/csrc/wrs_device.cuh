@@ -248,31 +248,6 @@ __device__ __forceinline__ void store_f(float* p, const float (&v)[N]) {
   *reinterpret_cast<typename VecF<N>::T*>(p) = t;
 }
 
-template <int N> struct VecH;
-template <> struct VecH<1> { using T = unsigned short; };
-template <> struct VecH<2> { using T = unsigned int; };
-template <> struct VecH<4> { using T = uint2; };
-
-template <int N>
-__device__ __forceinline__ void load_h(const __half* p, float (&v)[N]) {
-  typename VecH<N>::T t = *reinterpret_cast<const typename VecH<N>::T*>(p);
-  const __half* th = reinterpret_cast<const __half*>(&t);
-#pragma unroll
-  for (int i = 0; i < N; ++i) v[i] = __half2float(th[i]);
-}
-
-template <bool F16, int N>
-__device__ __forceinline__ void load_colv(const void* base, int64_t off, float (&v)[N]) {
-  if constexpr (F16) load_h<N>(static_cast<const __half*>(base) + off, v);
-  else load_f<N>(static_cast<const float*>(base) + off, v);
-}
-
-template <bool F16>
-__device__ __forceinline__ void store_col(void* base, int64_t off, float v) {
-  if constexpr (F16) static_cast<__half*>(base)[off] = __float2half_rn(v);
-  else static_cast<float*>(base)[off] = v;
-}
-
 // Weight and colour of slot j for a group of N pixels whose first entry is at
 // `at` in planes of `stride` entries. FP32 colour: one float4 record
 // {w, r, g, b} per entry in `col`; FP16 colour: a weight plane and an 8-byte

@@ -129,3 +129,16 @@ def test_foveate_host_checks_before_any_cuda_call(lib):
     assert lib.wrs_mip_build(None, 48, 16, 8, 3, fake, 4096, None) == _lib.WRS_ERR_ARG
     assert lib.wrs_mip_build(fake, 48, 16, 8, 3, C.c_void_p((1 << 20) + 16), 4096,
                              None) == _lib.WRS_ERR_ARG
+
+
+def test_host_paths_check_arguments_before_any_cuda_call(lib):
+    assert lib.wrs_host_pipe_stage_bytes(None, 0) == 0
+    out = C.c_void_p()
+    assert lib.wrs_host_pipe_create(None, C.c_void_p(1 << 20), 1 << 20, 0, C.byref(out)) == _lib.WRS_ERR_ARG
+    assert lib.wrs_host_pipe_push(None, None, 0.0, 0.0, None, None) == _lib.WRS_ERR_ARG
+    assert lib.wrs_host_pipe_finish(None) == _lib.WRS_ERR_ARG
+    assert lib.wrs_host_pipe_destroy(None) == _lib.WRS_OK
+    assert lib.wrs_push_frame_host_noalloc(None, None, 0.0, 0.0, None, None, None) == _lib.WRS_ERR_ARG
+    assert b"context" in lib.wrs_last_error()
+    text = open(_lib.HEADER).read()
+    assert "#define WRS_NOALLOC_MAX_PIXELS 8294400" in text
