@@ -549,12 +549,16 @@ def run_reprojection(args, dev):
 
 def run_serving(args, dev):
     """The 64-viewer serving trace at the workload's frame rates (72-120 Hz per
-    viewer) and at an overload (200-300 Hz), batched vs one launch per frame."""
+    viewer) and at an overload (200-300 Hz), batched vs one launch per frame;
+    then the workload's rates with every frame foveated on the device from the
+    viewer's rendered image (requests carry only a gaze)."""
     from paper_2510_03964_gb300 import serve
     out = {}
-    for name, rate in (("rates_72_120hz", (72.0, 120.0)), ("overload_200_300hz", (200.0, 300.0))):
+    for name, rate, source in (("rates_72_120hz", (72.0, 120.0), "frames"),
+                               ("overload_200_300hz", (200.0, 300.0), "frames"),
+                               ("rates_72_120hz_foveated_on_device", (72.0, 120.0), "render")):
         out[name] = serve.serve_compare(n_viewers=64, duration_s=args.serve, budget_gb=60.0, seed=0,
-                                        device=dev, rate_hz=rate)
+                                        device=dev, rate_hz=rate, source=source)
         torch.cuda.empty_cache()
     return out
 

@@ -21,6 +21,14 @@ Two dispatch modes run the same arrival trace:
 A frame's latency is the time from its arrival to the host observing its
 launch's completion event. Results per frame are identical in both modes and
 to a viewer served alone (each viewer's frames are applied in arrival order).
+
+Frames come from one of two sources: a ``FramePool`` of foveated frames made
+beforehand, or a ``RenderPool`` holding each resolution class's rendered
+image and its mip levels on the device, from which every request's frame is
+foveated on the device for that request's gaze (Sec. 4.3's post-process): in
+plain mode inside the update kernel (wrs_push_foveated), in batched mode by
+one foveation launch per frame into the viewer's frame buffer ahead of the
+batched update. Either way a request carries only a gaze.
 """
 from __future__ import annotations
 
@@ -32,7 +40,7 @@ import time
 import numpy as np
 import torch
 
-from .wrs import Batch, Stream, make_config, state_bytes
+from .wrs import Batch, Foveation, Stream, foveate, make_config, state_bytes
 
 # resolution classes of the mixed-viewer workload: (width, height, ring radii)
 CLASSES = ((3840, 2160, (200.0, 500.0, 1000.0)), (2064, 2208, (200.0, 500.0, 1000.0)),
@@ -116,6 +124,25 @@ class FramePool:
         return self.frames[cls][i], self.gaze[cls][i]
 
 
+class RenderPool:
+    """Each resolution class's rendered image and mip levels, resident on the
+    device, and a gaze path per class; viewer frame t is foveated on the device
+    from its class's image for gaze t mod F."""
+
+    def __init__(self, classes, frames_per_class: int, device, seed: int = 0, filter: str = "bilinear"):
+        from synth import gaze_path, ground_truth  # input generator, not part of the method
+        self.fov, self.gaze = [], []
+        for ci, (w, h, radii) in enumerate(classes):
+            img = torch.from_numpy(ground_truth(w, h, seed + ci)).to(device)
+            self.fov.append(Foveation(img, radii, filter=filter))
+            self.gaze.append(gaze_path(w, h, frames_per_class, seed=seed + ci))
+        self.F = frames_per_class
+
+    def get(self, cls: int, t: int):
+        i = t % self.F
+        return self.fov[cls], self.gaze[cls][i]
+
+
 @dataclasses.dataclass
 class ServeStats:
     mode: str
@@ -178,6 +205,8 @@ class Server:
         self.live = {}            # vid -> Stream
         self.pushed = collections.defaultdict(list)  # vid -> frame counters pushed, in order
         self.kept = {}            # vid -> Stream kept after leaving (keep_states)
+        self.render = isinstance(pool, RenderPool)
+        self.frame_buf = {}       # vid -> device frame the batched mode foveates into
 
     # -- admission ---------------------------------------------------------
     def _admit(self, vid) -> bool:
@@ -192,6 +221,9 @@ class Server:
         self.init_ev[vid] = ev
         self.live[vid] = st
         self.used += need
+        if self.render and self.mode == "batched":
+            self.frame_buf[vid] = torch.empty((v.height, v.width, 3), dtype=torch.float32,
+                                              device=self.device)
         return True
 
     def _ready(self, vid, stream):
@@ -202,6 +234,7 @@ class Server:
 
     def _release(self, vid):
         self.init_ev.pop(vid, None)
+        self.frame_buf.pop(vid, None)
         st = self.live.pop(vid)
         self.used -= self.specs[vid].state_bytes()
         if self.keep_states:
@@ -292,12 +325,18 @@ class Server:
                         t = next_t[vid]
                         next_t[vid] += 1
                         fr, gz = self.pool.get(self.specs[vid].cls, t)
+                        self._ready(vid, stream)
+                        if self.render:
+                            # foveate this request's frame on the device first
+                            src, buf = fr, self.frame_buf[vid]
+                            foveate(src.img, src.mip, src.radii, gz, src.filter, out=buf,
+                                    want_ring_map=False, stream=stream)
+                            fr = buf
                         sts.append(self.live[vid])
                         frs.append(fr)
                         gzs.append(gz)
                         frames.append((vid, ta))
                         busy[vid] += 1
-                        self._ready(vid, stream)
                         self.pushed[vid].append(t)
                     self.batches[si].push(sts, frs, gzs, stream=stream)
                     ev = torch.cuda.Event()
@@ -314,7 +353,10 @@ class Server:
                         next_t[vid] += 1
                         fr, gz = self.pool.get(self.specs[vid].cls, t)
                         self._ready(vid, stream)
-                        self.live[vid].push_frame(fr, gz, stream=stream)
+                        if self.render:
+                            self.live[vid].push_foveated(fr, gz, stream=stream)
+                        else:
+                            self.live[vid].push_frame(fr, gz, stream=stream)
                         busy[vid] += 1
                         ev = torch.cuda.Event()
                         ev.record(stream)
@@ -347,20 +389,27 @@ def replay_alone(spec: ViewerSpec, pushed, pool: FramePool, device=None) -> Stre
                 color_fp16=spec.color_fp16, device=device)
     for t in pushed:
         fr, gz = pool.get(spec.cls, t)
-        st.push_frame(fr, gz)
+        if isinstance(pool, RenderPool):
+            st.push_foveated(fr, gz)
+        else:
+            st.push_frame(fr, gz)
     return st
 
 
 def serve_compare(n_viewers=64, duration_s=10.0, budget_gb=60.0, seed=0, frames_per_class=8,
                   device=None, rate_hz=(72.0, 120.0), batch_launch=None, classes=CLASSES,
-                  n_streams=4, depth=2) -> dict:
-    """Both modes on the same trace; returns their summaries."""
+                  n_streams=4, depth=2, source="frames") -> dict:
+    """Both modes on the same trace; returns their summaries. source: "frames"
+    (foveated beforehand) or "render" (foveated on the device per request)."""
     dev = torch.device("cuda") if device is None else torch.device(device)
     specs = viewer_mix(n_viewers, duration_s, seed, rate_hz, classes)
     trace = arrivals(specs, seed)
-    pool = FramePool(classes, frames_per_class, dev, seed)
+    if source == "render":
+        pool = RenderPool(classes, frames_per_class, dev, seed)
+    else:
+        pool = FramePool(classes, frames_per_class, dev, seed)
     out = {"viewers": n_viewers, "duration_s": duration_s, "budget_gb": budget_gb,
-           "rate_hz": list(rate_hz), "frames_offered": len(trace),
+           "rate_hz": list(rate_hz), "frames_offered": len(trace), "source": source,
            "batched_streams": n_streams, "batched_depth": depth}
     for mode in ("batched", "plain"):
         srv = Server(specs, pool, int(budget_gb * 1e9), mode=mode, n_streams=n_streams, depth=depth,

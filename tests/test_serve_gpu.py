@@ -12,12 +12,16 @@ pytestmark = pytest.mark.gpu
 SMALL = ((64, 32, (6.0, 15.0)), (96, 40, (8.0, 20.0)), (128, 24, (10.0, 25.0)), (32, 16, (4.0, 10.0)))
 
 
+@pytest.mark.parametrize("source", ["frames", "render"])
 @pytest.mark.parametrize("mode", ["batched", "plain"])
-def test_served_viewers_equal_alone(mode):
+def test_served_viewers_equal_alone(mode, source):
+    # "render": every request's frame is foveated on the device from its
+    # class's image (foveate + batched update, or the update foveating on read)
     dev = torch.device("cuda")
     specs = serve.viewer_mix(12, 1.5, seed=1, rate_hz=(150.0, 300.0), classes=SMALL)
     trace = serve.arrivals(specs, seed=1)
-    pool = serve.FramePool(SMALL, 6, dev, seed=1)
+    pool = (serve.RenderPool(SMALL, 6, dev, seed=1) if source == "render"
+            else serve.FramePool(SMALL, 6, dev, seed=1))
     srv = serve.Server(specs, pool, budget_bytes=10**10, mode=mode, device=dev, keep_states=True)
     stats = srv.run(trace, 1.5)
     s = stats.summary()
