@@ -205,7 +205,8 @@ int wrs_host_pipe_create(wrs_ctx* ctx, void* d_stage, size_t bytes, int with_fov
  * are in flight and the host buffers of frame n-2 and older are free again.
  * h_frame, h_fov_map (nullable) and h_out of the last two frames must stay
  * valid and unmodified until wrs_host_pipe_finish (pinned host memory makes
- * the copies asynchronous). Errors: as wrs_push_frame, WRS_ERR_CUDA. */
+ * the copies asynchronous). The context's device must be current. Errors: as
+ * wrs_push_frame, WRS_ERR_ARG for another current device, WRS_ERR_CUDA. */
 int wrs_host_pipe_push(wrs_host_pipe* p, const float* h_frame, float gaze_x, float gaze_y,
                        const uint8_t* h_fov_map, float* h_out);
 

@@ -25,6 +25,17 @@ namespace {
 
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
+// The pipeline's streams belong to the context's device: it must be current.
+int check_device(const wrs_ctx* x, const char* what) {
+  int cur = -1;
+  const cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return wrs_cuda_fail(e, what);
+  if (cur != x->device)
+    return wrs_fail(WRS_ERR_ARG, "%s: the stream's device (%d) must be current (is %d)", what,
+                    x->device, cur);
+  return WRS_OK;
+}
+
 void destroy_handles(wrs_host_pipe* p) {
   for (int i = 0; i < 2; ++i) {
     if (p->in_done[i]) cudaEventDestroy(p->in_done[i]);
@@ -53,6 +64,7 @@ extern "C" int wrs_host_pipe_create(wrs_ctx* x, void* d_stage, size_t bytes, int
   if (with_fov != 0 && with_fov != 1) return wrs_fail(WRS_ERR_ARG, "with_fov must be 0 or 1");
   if (!d_stage || reinterpret_cast<uintptr_t>(d_stage) % 256 != 0)
     return wrs_fail(WRS_ERR_ARG, "d_stage is NULL or not 256-byte aligned");
+  if (int rc = check_device(x, "wrs_host_pipe_create")) return rc;
   const size_t need = wrs_host_pipe_stage_bytes(x, with_fov);
   if (bytes < need)
     return wrs_fail(WRS_ERR_BUDGET, "stage holds %zu bytes, the pipeline needs %zu", bytes, need);
@@ -96,6 +108,7 @@ extern "C" int wrs_host_pipe_push(wrs_host_pipe* p, const float* h_frame, float 
     return wrs_fail(WRS_ERR_ARG, "this pipeline was created without fov-map slots");
   const int s = static_cast<int>(p->n & 1u);
   wrs_ctx* x = p->x;
+  if (int rc = check_device(x, "wrs_host_pipe_push")) return rc;
   const size_t hw = static_cast<size_t>(x->cfg.width) * x->cfg.height;
   cudaError_t e = cudaSuccess;
   // frame n-2 used this slot: its output must have reached the host
