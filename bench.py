@@ -5,7 +5,9 @@ Workload: 3840x2160 RGB, K = 8 slots, FP32 colour planes (``--workload 4k``;
 from fixations + saccades, 240 distinct synthetic frames resident in HBM and
 pushed cyclically. One step = one frame pushed through the whole per-pixel
 path (weight, key, temporal bias, K-slot combine, resolve) = one kernel
-launch. The state (1.9 GB per frame touched) is far larger than the 129 MB
+launch. The stream first runs one untimed pass of its 240 frames (reported
+as ``first_pass``), so the timed frames sit at the same age of the stream
+whatever --steps and --warmup are. The state (1.9 GB per frame touched) is far larger than the 129 MB
 L2, so no flush is needed between steps.
 
 Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle
@@ -602,9 +604,31 @@ def run_ours(args, world, rank, local):
     def push(t):
         st.push_frame(frames[t % nfr], gaze[t % nfr], None, out, stream=stream)
 
+    # The stream's age sets its replacement rate (every pixel inserts in the
+    # first K frames, then the rate falls as the history's weight grows), so
+    # the stream first runs one untimed pass of the workload's frame sequence:
+    # the timed frames then sit at the same point of a running stream whatever
+    # --steps and --warmup are. That pass is timed on its own as the cost of a
+    # fresh stream's first frames.
+    age = spec.frames if args.age < 0 else args.age
+    first_pass = None
+    if age > 0:
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        r0 = st.replacements(stream=stream)
+        with torch.cuda.stream(stream):
+            a0.record(stream)
+            for t in range(age):
+                push(t)
+            a1.record(stream)
+        torch.cuda.synchronize()
+        first_pass = {"frames": age, "ms_per_frame": round(a0.elapsed_time(a1) / age, 4),
+                      "replacement_rate": round((st.replacements(stream=stream) - r0) / float(hw * age), 4),
+                      "note": "a fresh stream's first frames, pushed back to back before the warm-up "
+                              "(untimed for value)"}
     with torch.cuda.stream(stream):
         for t in range(args.warmup):
-            push(t)
+            push(age + t)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local) if rank == 0 else None
@@ -617,7 +641,7 @@ def run_ours(args, world, rank, local):
     with torch.cuda.stream(stream):
         for i in range(args.steps):
             starts[i].record(stream)
-            push(args.warmup + i)
+            push(age + args.warmup + i)
             ends[i].record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -730,6 +754,8 @@ def run_ours(args, world, rank, local):
                                    f"device over the timed frames) x {replacement_bytes(spec.color_fp16, lit)} B",
                      "kernel": kname},
         "replacement_rate": round(rho, 4),
+        "stream_age_frames": age + args.warmup,
+        "first_pass": first_pass,
         "pct_nominal_8tbs": round(100 * achieved / 8000.0, 2),
         "gpu_launches": args.steps,
         "clocks": clk,
@@ -760,6 +786,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="4k",
                     choices=["4k", "4k_fp16", "hd", "hd_k8", "tiny", "4k_k1", "4k_k1_literal", "4k_bias2"])
+    ap.add_argument("--age", type=int, default=-1,
+                    help="untimed frames pushed before the warm-up (default: one pass of the "
+                         "workload's frame sequence)")
     ap.add_argument("--distinct-frames", type=int, default=0,
                     help="frames resident in HBM (default: all of the workload's)")
     ap.add_argument("--pipe", type=int, default=1, help="1: pipelined kernel (default), 0: plain")
