@@ -137,9 +137,15 @@ def recorded_traffic(kernel: str, workload_name: str):
 # ------------------------------------------------------------------ oracle timing
 
 def oracle_ms_per_frame(spec, pixels: np.ndarray, frames: int, nthreads: int,
-                        fv_dev: Foveator, gaze: np.ndarray, budget_s: float | None = None):
+                        fv_dev: Foveator, gaze: np.ndarray, budget_s: float | None = None,
+                        gpu_out=None):
     """Times the oracle on a fixed sample of pixels (every pixel is an
-    independent stream) and scales the mean per-frame time to a full frame."""
+    independent stream) and scales the mean per-frame time to a full frame.
+
+    gpu_out(t, gaze): if given, the GPU's resolved colours of frame t at the
+    sampled pixels ([n, 3] float64, from a fresh stream fed the same frames);
+    they are compared, outside the timed part, with the oracle's FP64 resolve
+    of the exact colours, and the errors are returned as a third value."""
     import oracle
     st = oracle.OracleStream(spec.width, spec.height, spec.K, spec.r_f, seed=spec.seed,
                              stream_id=spec.stream_id, temporal_bias=spec.temporal_bias,
@@ -148,19 +154,42 @@ def oracle_ms_per_frame(spec, pixels: np.ndarray, frames: int, nthreads: int,
     flat = host.reshape(-1, 3)
     pix_t = torch.as_tensor(pixels)
     times = []
+    err = {"max_abs": 0.0, "max_rel": 0.0, "sum_rel": 0.0, "n": 0, "excess": -np.inf}
+    rtol = 2.0 ** -11 if spec.color_fp16 else 1e-5
     t_start = time.perf_counter()
     for t in range(frames):
         gx, gy = gaze[t % len(gaze)]
         flat[pixels] = frame_pixels(fv_dev, float(gx), float(gy), pix_t).cpu().numpy()
         t0 = time.perf_counter()
         st.push_frame(host, (gx, gy))
-        st.resolve()
+        ref = st.resolve()
         times.append(time.perf_counter() - t0)
+        if gpu_out is not None:
+            got = gpu_out(t, gaze[t % len(gaze)])
+            d = np.abs(got - ref)
+            big = np.abs(ref) > 1e-6
+            rel = d[big] / np.abs(ref[big])
+            err["max_abs"] = max(err["max_abs"], float(d.max()))
+            if rel.size:
+                err["max_rel"] = max(err["max_rel"], float(rel.max()))
+                err["sum_rel"] += float(rel.sum())
+                err["n"] += int(rel.size)
+            err["excess"] = max(err["excess"], float((d - (rtol * np.abs(ref) + 1e-7)).max()))
         if budget_s is not None and time.perf_counter() - t_start > budget_s and t >= 3:
             break
     steady = times[1:] if len(times) > 1 else times
     per_frame = statistics.mean(steady) * (spec.width * spec.height) / len(pixels)
-    return per_frame * 1e3, len(times)
+    if gpu_out is None:
+        return per_frame * 1e3, len(times)
+    summary = {"reference": "the oracle's FP64 resolve of the exact FP32 colours",
+               "colour_storage": "fp16" if spec.color_fp16 else "fp32",
+               "frames": len(times), "pixels": int(len(pixels)),
+               "max_abs": float(f"{err['max_abs']:.4g}"), "max_rel": float(f"{err['max_rel']:.4g}"),
+               "mean_rel": float(f"{err['sum_rel'] / max(1, err['n']):.4g}"),
+               "rel_over": "components with |ref| > 1e-6",
+               "tolerance": f"|gpu - ref| <= {'2^-11' if spec.color_fp16 else '1e-5'} |ref| + 1e-7",
+               "within_tolerance": bool(err["excess"] <= 0.0)}
+    return per_frame * 1e3, len(times), summary
 
 
 def sample_pixels(spec, n: int) -> np.ndarray:
@@ -768,8 +797,28 @@ def run_ours(args, world, rank, local):
     if args.cpu_baseline:
         nthreads = os.cpu_count() or 1
         pixels = sample_pixels(spec, args.cpu_sample)
-        ms_cpu, n_cpu_frames = oracle_ms_per_frame(spec, pixels, spec.frames, nthreads, fv, gaze,
-                                          budget_s=args.cpu_budget_s)
+        # a fresh GPU stream fed the same frames: its resolved colours at the
+        # sampled pixels against the oracle's FP64 resolve (precision per config)
+        st_err = wrs.Stream(spec.width, spec.height, spec.K, spec.r_f, seed=seed,
+                            stream_id=spec.stream_id, color_fp16=spec.color_fp16,
+                            temporal_bias=spec.temporal_bias, device=dev, stream=stream,
+                            update_rule=spec.update_rule)
+        buf = torch.empty((spec.height, spec.width, 3), dtype=torch.float32, device=dev)
+        pix_d = torch.as_tensor(pixels, device=dev)
+
+        def gpu_out(t, g):
+            with torch.cuda.stream(stream):
+                fv.frame(float(g[0]), float(g[1]), out=buf)
+                st_err.push_frame(buf, g, None, out, stream=stream)
+                sel = out.view(-1, 3)[pix_d].double()
+            torch.cuda.synchronize()
+            return sel.cpu().numpy()
+
+        ms_cpu, n_cpu_frames, res_err = oracle_ms_per_frame(
+            spec, pixels, spec.frames, nthreads, fv, gaze, budget_s=args.cpu_budget_s,
+            gpu_out=gpu_out)
+        st_err.close()
+        line["resolve_error"] = res_err
         line["cpu_baseline"] = {
             "value": round(ms_cpu, 3), "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"{len(pixels)} of {hw} pixels (every {hw // len(pixels)}th), {n_cpu_frames} frames, "
