@@ -851,8 +851,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=131072)
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--ref-sample", type=int, default=65536)
-    ap.add_argument("--batch-warmup", type=int, default=100,
-                    help="untimed rounds before the timed ones (the streams' reservoirs fill first)")
+    ap.add_argument("--batch-warmup", type=int, default=240,
+                    help="untimed rounds before the timed ones: one pass of the workload's 240 "
+                         "frames, the stream age of the single-stream line's timed frames")
     ap.add_argument("--batch-rounds", type=int, default=200,
                     help="rounds of the 16-stream batched workload (0 skips it)")
     ap.add_argument("--fov-reps", type=int, default=50,

@@ -180,14 +180,14 @@ int wrs_push_frame_host_noalloc(wrs_ctx* ctx, const float* h_frame, float gaze_x
 
 /* Pipelined host-buffer frames: the upload of frame n, the update of frame
  * n-1 and the download of frame n-2's resolved output overlap on three CUDA
- * streams the pipeline owns, through two device staging slots for frames and
- * outputs (and fov maps) in a caller-owned buffer. Each frame gets the same
+ * streams the pipeline owns, through three device staging slots for frames
+ * and outputs (and fov maps) in a caller-owned buffer. Each frame gets the same
  * update and output as wrs_push_frame_host. Not a step of the paper's method:
  * it moves frames between host memory and the device. */
 typedef struct wrs_host_pipe wrs_host_pipe;
 
-/* Device staging bytes the pipeline needs: two frames and two outputs of
- * width * height RGB floats (and two width * height fov maps if with_fov),
+/* Device staging bytes the pipeline needs: three frames and three outputs of
+ * width * height RGB floats (and three width * height fov maps if with_fov),
  * each 256-byte aligned. 0 for a NULL context. */
 size_t wrs_host_pipe_stage_bytes(const wrs_ctx* ctx, int with_fov);
 
@@ -201,9 +201,9 @@ int wrs_host_pipe_create(wrs_ctx* ctx, void* d_stage, size_t bytes, int with_fov
 /* Enqueues one frame: h_frame [height][width][3] floats is uploaded
  * asynchronously, the context's update and fused resolve run, and the
  * resolved frame is downloaded to h_out asynchronously. Before enqueuing
- * frame n the call waits until frame n-2 is complete, so at most two frames
- * are in flight and the host buffers of frame n-2 and older are free again.
- * h_frame, h_fov_map (nullable) and h_out of the last two frames must stay
+ * frame n the call waits until frame n-3 is complete, so at most three frames
+ * are in flight and the host buffers of frame n-3 and older are free again.
+ * h_frame, h_fov_map (nullable) and h_out of the last three frames must stay
  * valid and unmodified until wrs_host_pipe_finish (pinned host memory makes
  * the copies asynchronous). The context's device must be current. Errors: as
  * wrs_push_frame, WRS_ERR_ARG for another current device, WRS_ERR_CUDA. */

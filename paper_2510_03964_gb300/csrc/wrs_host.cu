@@ -1,23 +1,30 @@
 // Pipelined host-buffer frames. On GB300 the host link moves about 200 GB/s
-// each way, so a 4K frame in (99.5 MB) and its resolved frame out take about
-// as long as the update itself. Three CUDA streams overlap them: the copy of
-// frame n in, the update of frame n-1 and the copy of frame n-2's output run
-// at once, through two device staging slots for frames and two for outputs.
-// Events order each slot's reuse; the host waits only for frame n-2 to be
-// fully done before it enqueues frame n, which bounds the frames in flight
-// to two and keeps the caller's host buffers of older frames free.
+// each way, so a 4K frame in (99.5 MB) and its resolved frame out each take
+// longer than the update itself. Three CUDA streams overlap them:
+// the copy of frame n in, the update of frame n-1 and the copy of frame n-2's
+// output run at once, through kDepth device staging slots for frames and for
+// outputs. Events order each slot's reuse; the host waits only for frame
+// n - kDepth to be fully done before it enqueues frame n, which bounds the
+// frames in flight to kDepth and keeps the caller's host buffers of older
+// frames free. With two slots the upload of frame n could not start before
+// frame n-2's download ended, so a frame cost (up + update + down) / 2, more
+// than the link alone; three slots leave the link as the bound.
 #include <new>
 
 #include "wrs_internal.h"
 
+namespace {
+constexpr int kDepth = 3;  // staging slots = frames in flight
+}  // namespace
+
 struct wrs_host_pipe {
   wrs_ctx* x;
   int with_fov;
-  float* d_frame[2];
-  float* d_out[2];
-  uint8_t* d_fov[2];
+  float* d_frame[kDepth];
+  float* d_out[kDepth];
+  uint8_t* d_fov[kDepth];
   cudaStream_t s_in, s_comp, s_out;
-  cudaEvent_t in_done[2], comp_done[2], out_done[2];
+  cudaEvent_t in_done[kDepth], comp_done[kDepth], out_done[kDepth];
   uint64_t n;  // frames enqueued
 };
 
@@ -37,7 +44,7 @@ int check_device(const wrs_ctx* x, const char* what) {
 }
 
 void destroy_handles(wrs_host_pipe* p) {
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kDepth; ++i) {
     if (p->in_done[i]) cudaEventDestroy(p->in_done[i]);
     if (p->comp_done[i]) cudaEventDestroy(p->comp_done[i]);
     if (p->out_done[i]) cudaEventDestroy(p->out_done[i]);
@@ -52,7 +59,7 @@ void destroy_handles(wrs_host_pipe* p) {
 extern "C" size_t wrs_host_pipe_stage_bytes(const wrs_ctx* x, int with_fov) {
   if (!x) return 0;
   const size_t hw = static_cast<size_t>(x->cfg.width) * x->cfg.height;
-  return 2 * (2 * round256(hw * 3 * sizeof(float)) + (with_fov ? round256(hw) : 0));
+  return kDepth * (2 * round256(hw * 3 * sizeof(float)) + (with_fov ? round256(hw) : 0));
 }
 
 extern "C" int wrs_host_pipe_create(wrs_ctx* x, void* d_stage, size_t bytes, int with_fov,
@@ -74,7 +81,7 @@ extern "C" int wrs_host_pipe_create(wrs_ctx* x, void* d_stage, size_t bytes, int
   p->with_fov = with_fov;
   const size_t hw = static_cast<size_t>(x->cfg.width) * x->cfg.height;
   uint8_t* b = static_cast<uint8_t*>(d_stage);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kDepth; ++i) {
     p->d_frame[i] = reinterpret_cast<float*>(b);
     b += round256(hw * 3 * sizeof(float));
     p->d_out[i] = reinterpret_cast<float*>(b);
@@ -85,7 +92,7 @@ extern "C" int wrs_host_pipe_create(wrs_ctx* x, void* d_stage, size_t bytes, int
   cudaError_t e = cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_comp, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking);
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+  for (int i = 0; i < kDepth && e == cudaSuccess; ++i) {
     e = cudaEventCreateWithFlags(&p->in_done[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->comp_done[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->out_done[i], cudaEventDisableTiming);
@@ -106,13 +113,13 @@ extern "C" int wrs_host_pipe_push(wrs_host_pipe* p, const float* h_frame, float 
   if (!h_frame || !h_out) return wrs_fail(WRS_ERR_ARG, "h_frame and h_out must be non-NULL");
   if (h_fov && !p->with_fov)
     return wrs_fail(WRS_ERR_ARG, "this pipeline was created without fov-map slots");
-  const int s = static_cast<int>(p->n & 1u);
+  const int s = static_cast<int>(p->n % kDepth);
   wrs_ctx* x = p->x;
   if (int rc = check_device(x, "wrs_host_pipe_push")) return rc;
   const size_t hw = static_cast<size_t>(x->cfg.width) * x->cfg.height;
   cudaError_t e = cudaSuccess;
-  // frame n-2 used this slot: its output must have reached the host
-  if (p->n >= 2) e = cudaEventSynchronize(p->out_done[s]);
+  // frame n - kDepth used this slot: its output must have reached the host
+  if (p->n >= kDepth) e = cudaEventSynchronize(p->out_done[s]);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->d_frame[s], h_frame, hw * 3 * sizeof(float), cudaMemcpyHostToDevice,
                         p->s_in);
@@ -139,8 +146,8 @@ extern "C" int wrs_host_pipe_finish(wrs_host_pipe* p) {
   wrs_clear_error();
   if (!p) return wrs_fail(WRS_ERR_ARG, "pipeline is NULL");
   cudaError_t e = cudaSuccess;
-  for (uint64_t k = p->n >= 2 ? p->n - 2 : 0; k < p->n && e == cudaSuccess; ++k)
-    e = cudaEventSynchronize(p->out_done[k & 1u]);
+  for (uint64_t k = p->n >= kDepth ? p->n - kDepth : 0; k < p->n && e == cudaSuccess; ++k)
+    e = cudaEventSynchronize(p->out_done[k % kDepth]);
   return e == cudaSuccess ? WRS_OK : wrs_cuda_fail(e, "wrs_host_pipe_finish");
 }
 

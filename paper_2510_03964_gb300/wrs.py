@@ -329,7 +329,7 @@ class Batch:
 class HostPipeline:
     """Frames in host memory through one stream with the upload of the next
     frame, the update of this one and the download of the previous output
-    overlapping (wrs_host_pipe_*). Host tensors should be pinned; the last two
+    overlapping (wrs_host_pipe_*). Host tensors should be pinned; the last three
     frames' buffers must stay untouched until finish()."""
 
     def __init__(self, stream: Stream, with_fov: bool = False):

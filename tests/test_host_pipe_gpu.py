@@ -43,26 +43,26 @@ def test_pipeline_equals_synchronous_host_path(with_fov, color_fp16):
     pipe.close()
 
 
-def test_pipeline_reuses_host_buffers_after_two_frames():
-    # the pipeline waits for frame n-2 before enqueuing frame n, so a caller
-    # cycling three host buffers never overwrites one still in flight
+def test_pipeline_reuses_host_buffers_after_three_frames():
+    # the pipeline waits for frame n-3 before enqueuing frame n, so a caller
+    # cycling four host buffers never overwrites one still in flight
     w, h, K = 64, 32, 4
     fv = Foveator(w, h, (6.0, 15.0), seed=5)
-    gz = gaze_path(w, h, 12, seed=5, model="jitter", jitter_px=5.0)
+    gz = gaze_path(w, h, 14, seed=5, model="jitter", jitter_px=5.0)
     a = wrs.Stream(w, h, K, 6.0, seed=6)
     b = wrs.Stream(w, h, K, 6.0, seed=6)
     pipe = wrs.HostPipeline(a)
-    ring_in = [torch.empty((h, w, 3)).pin_memory() for _ in range(3)]
-    ring_out = [torch.empty((h, w, 3)).pin_memory() for _ in range(3)]
+    ring_in = [torch.empty((h, w, 3)).pin_memory() for _ in range(4)]
+    ring_out = [torch.empty((h, w, 3)).pin_memory() for _ in range(4)]
     d_in = torch.empty((h, w, 3), device="cuda")
     d_out = torch.empty((h, w, 3), device="cuda")
-    for t in range(12):
-        if t >= 3:
-            # frame t-3's output is complete: check it before its buffer is reused
+    for t in range(14):
+        if t >= 4:
+            # frame t-4's output is complete: check it before its buffer is reused
             ref = torch.empty((h, w, 3)).pin_memory()
-            b.push_frame_host(fv.frame(*gz[t - 3])[0].contiguous(), gz[t - 3], ref, d_in, d_out)
-            assert torch.equal(ring_out[t % 3].view(torch.int32), ref.view(torch.int32)), f"frame {t - 3}"
-        ring_in[t % 3].copy_(fv.frame(*gz[t])[0])
-        pipe.push(ring_in[t % 3], gz[t], ring_out[t % 3])
+            b.push_frame_host(fv.frame(*gz[t - 4])[0].contiguous(), gz[t - 4], ref, d_in, d_out)
+            assert torch.equal(ring_out[t % 4].view(torch.int32), ref.view(torch.int32)), f"frame {t - 4}"
+        ring_in[t % 4].copy_(fv.frame(*gz[t])[0])
+        pipe.push(ring_in[t % 4], gz[t], ring_out[t % 4])
     pipe.finish()
     pipe.close()
