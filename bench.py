@@ -35,6 +35,14 @@ from synth import Foveator, frame_pixels, gaze_path, workload  # noqa: E402
 
 METRIC = "4K reservoir update+resolve ms/frame, % HBM peak; served p99 latency vs plain"
 UNIT = "ms/frame"
+# The paper's own figure for this pass, as context: another GPU, a pixel shader
+# inside a game engine, one slot per pixel (the introduction states the 4K
+# figure; the runtime evaluation names the hardware and gives whole-frame times).
+PAPER_CONTEXT = {"value": "< 1", "unit": "ms/frame", "resolution": "4K",
+                 "hardware": "NVIDIA RTX 4070 Ti Super, Intel i9-12900K",
+                 "implementation": "HLSL pixel shader in Unity 6 (Built-In pipeline), reservoir size n = 1",
+                 "note": "context, not the target: measured as whole-frame time over foveated rendering "
+                         "alone, under 0.1 ms in three of four scenes and 0.94 ms in the fourth"}
 
 
 def algorithmic_bytes_per_px(K: int, fp16: bool, literal: bool = False) -> int:
@@ -782,6 +790,7 @@ def run_ours(args, world, rank, local):
                                    f"by every pixel-update + replacement rate {rho:.4f} (counted on the "
                                    f"device over the timed frames) x {replacement_bytes(spec.color_fp16, lit)} B",
                      "kernel": kname},
+        "paper": PAPER_CONTEXT,
         "replacement_rate": round(rho, 4),
         "stream_age_frames": age + args.warmup,
         "first_pass": first_pass,
