@@ -14,7 +14,9 @@ Two dispatch modes run the same arrival trace:
   viewers with a pending frame contributes its oldest one to one persistent
   batched launch (wrs_push_batch, a CUDA-graph kernel node); frames that
   arrive while launches run join the next one. Batches on different streams
-  overlap on the device.
+  overlap on the device. A launch that would hold a single frame goes out as
+  that viewer's own update (wrs_push_frame, or wrs_push_foveated for rendered
+  frames) instead: a batch of one gains nothing and costs the graph update.
 * ``plain``: every frame is launched on its own (wrs_push_frame) as soon as it
   arrives, on one stream.
 
@@ -155,6 +157,7 @@ class ServeStats:
     viewers_admitted: int
     viewers_queued_max: int
     peak_state_bytes: int
+    single_launches: int = 0  # batched mode: launches that held one frame (the viewer's own kernel)
 
     def summary(self) -> dict:
         lat = sorted(self.latencies_ms)
@@ -170,6 +173,7 @@ class ServeStats:
                 "mean_ms": round(statistics.mean(lat), 3) if lat else None,
                 "mpx_updates_per_s": round(self.pixel_updates / self.duration_s / 1e6, 1),
                 "launches": self.launches, "frames_per_launch": round(self.frames_served / max(1, self.launches), 2),
+                "single_frame_launches": self.single_launches,
                 "viewers_admitted": self.viewers_admitted, "viewers_queued_max": self.viewers_queued_max,
                 "peak_state_gb": round(self.peak_state_bytes / 1e9, 2)}
 
@@ -179,13 +183,14 @@ class Server:
 
     def __init__(self, specs, pool: FramePool, budget_bytes: int, mode: str = "batched",
                  n_streams: int = 2, depth: int = 2, device=None, keep_states: bool = False,
-                 batch_launch=None):
+                 batch_launch=None, single_direct: bool = True):
         assert mode in ("batched", "plain")
         self.specs = {v.vid: v for v in specs}
         self.pool = pool
         self.budget = int(budget_bytes)
         self.mode = mode
         self.depth = depth
+        self.single_direct = single_direct
         self.device = torch.device("cuda") if device is None else torch.device(device)
         self.keep_states = keep_states
         n_streams = n_streams if mode == "batched" else 1
@@ -256,7 +261,7 @@ class Server:
         leaving = set()
         inflight = []         # (event, stream index, [(vid, arrival_s)])
         queued = collections.Counter()  # stream index -> launches in flight
-        lat, served, rejected, pix, launches = [], 0, 0, 0, 0
+        lat, served, rejected, pix, launches, singles = [], 0, 0, 0, 0, 0
         admitted_total, queued_max, peak = 0, 0, 0
         t0 = time.perf_counter()
         while True:
@@ -319,6 +324,27 @@ class Server:
                     ready = ready[:self.batches[si].max_streams]
                     if not ready:
                         continue
+                    if self.single_direct and len(ready) == 1:
+                        # a batch of one: the viewer's own update on its stream
+                        vid = ready[0]
+                        ta = pending[vid].popleft()
+                        t = next_t[vid]
+                        next_t[vid] += 1
+                        fr, gz = self.pool.get(self.specs[vid].cls, t)
+                        self._ready(vid, stream)
+                        if self.render:
+                            self.live[vid].push_foveated(fr, gz, stream=stream)
+                        else:
+                            self.live[vid].push_frame(fr, gz, stream=stream)
+                        busy[vid] += 1
+                        self.pushed[vid].append(t)
+                        ev = torch.cuda.Event()
+                        ev.record(stream)
+                        inflight.append((ev, si, [(vid, ta)]))
+                        queued[si] += 1
+                        launches += 1
+                        singles += 1
+                        continue
                     sts, frs, gzs, frames = [], [], [], []
                     for vid in ready:
                         ta = pending[vid].popleft()
@@ -372,7 +398,7 @@ class Server:
         for vid in list(self.live):
             self._release(vid)
         return ServeStats(self.mode, max(elapsed, duration_s), served, rejected, pix, lat, launches,
-                          admitted_total, queued_max, peak)
+                          admitted_total, queued_max, peak, singles)
 
     def close(self):
         for b in self.batches:
@@ -398,7 +424,7 @@ def replay_alone(spec: ViewerSpec, pushed, pool: FramePool, device=None) -> Stre
 
 def serve_compare(n_viewers=64, duration_s=10.0, budget_gb=60.0, seed=0, frames_per_class=8,
                   device=None, rate_hz=(72.0, 120.0), batch_launch=None, classes=CLASSES,
-                  n_streams=4, depth=2, source="frames") -> dict:
+                  n_streams=4, depth=3, source="frames") -> dict:
     """Both modes on the same trace; returns their summaries. source: "frames"
     (foveated beforehand) or "render" (foveated on the device per request)."""
     dev = torch.device("cuda") if device is None else torch.device(device)

@@ -13,22 +13,27 @@ SMALL = ((64, 32, (6.0, 15.0)), (96, 40, (8.0, 20.0)), (128, 24, (10.0, 25.0)), 
 
 
 @pytest.mark.parametrize("source", ["frames", "render"])
-@pytest.mark.parametrize("mode", ["batched", "plain"])
-def test_served_viewers_equal_alone(mode, source):
+@pytest.mark.parametrize("mode,single_direct", [("batched", True), ("batched", False), ("plain", True)])
+def test_served_viewers_equal_alone(mode, single_direct, source):
     # "render": every request's frame is foveated on the device from its
-    # class's image (foveate + batched update, or the update foveating on read)
+    # class's image (foveate + batched update, or the update foveating on read).
+    # single_direct: a launch of one frame is the viewer's own update, or
+    # (False) every launch is a batch, even of one.
     dev = torch.device("cuda")
     specs = serve.viewer_mix(12, 1.5, seed=1, rate_hz=(150.0, 300.0), classes=SMALL)
     trace = serve.arrivals(specs, seed=1)
     pool = (serve.RenderPool(SMALL, 6, dev, seed=1) if source == "render"
             else serve.FramePool(SMALL, 6, dev, seed=1))
-    srv = serve.Server(specs, pool, budget_bytes=10**10, mode=mode, device=dev, keep_states=True)
+    srv = serve.Server(specs, pool, budget_bytes=10**10, mode=mode, device=dev, keep_states=True,
+                       single_direct=single_direct)
     stats = srv.run(trace, 1.5)
     s = stats.summary()
     assert stats.frames_served + stats.frames_rejected == len(trace)
     assert stats.frames_served > 0 and s["p99_ms"] >= s["p50_ms"] > 0
     if mode == "batched":
         assert s["frames_per_launch"] >= 1.0
+        if not single_direct:
+            assert s["single_frame_launches"] == 0
     for vid, st in srv.kept.items():
         alone = serve.replay_alone(srv.specs[vid], srv.pushed[vid], pool, device=dev)
         torch.cuda.synchronize()
