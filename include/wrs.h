@@ -93,13 +93,18 @@ typedef struct {
  *   FP32 colour: rec[j] float4 {w, r, g, b} at col_off + j*plane_bytes_col
  *                (plane_bytes_col = 16*plane_px; wt_off = -1). One record per
  *                slot keeps a replacement's writes in one 16-byte entry.
- *   FP16 colour: wt[j] float at wt_off + j*plane_bytes4 and rec[j], 8-byte records
- *                {r, g, b, 0} of IEEE halves, at col_off + j*plane_bytes_col
- *                (plane_bytes_col = 8*plane_px). */
+ *   FP16 colour: rec[j], 8-byte records {r, g, b, w_hi} at col_off +
+ *                j*plane_bytes_col (plane_bytes_col = 8*plane_px): the colour as
+ *                IEEE halves and the high 16 bits of the FP32 weight w; wlo[j]
+ *                uint16 at wt_off + j*plane_bytes_wt (plane_bytes_wt =
+ *                2*plane_px) holds its low 16 bits, so w's bits are
+ *                (w_hi << 16) | wlo. col_off is wt_off + K*plane_bytes_wt rounded
+ *                up to 256 bytes. */
 typedef struct {
   int64_t plane_px;
   int64_t plane_bytes4;     /* plane_px * 4 */
-  int64_t plane_bytes_col;  /* plane_px * 4 (FP32 colour) or * 2 (FP16 colour) */
+  int64_t plane_bytes_col;  /* plane_px * 16 (FP32 colour) or * 8 (FP16 colour) */
+  int64_t plane_bytes_wt;   /* plane_px * 2 (FP16 colour) or 0 (FP32 colour) */
   int64_t status_off;       /* 256-byte header: uint32 status word (WRS_OK or WRS_ERR_TIMEOUT)
                                at +0, uint64 count of slot replacements at +8 */
   int64_t W_off, P_off, key_off, idx_off, wt_off, col_off;

@@ -25,7 +25,7 @@ class WrsConfig(C.Structure):
 
 class WrsLayout(C.Structure):
     _fields_ = [("plane_px", C.c_int64), ("plane_bytes4", C.c_int64), ("plane_bytes_col", C.c_int64),
-                ("status_off", C.c_int64), ("W_off", C.c_int64), ("P_off", C.c_int64),
+                ("plane_bytes_wt", C.c_int64), ("status_off", C.c_int64), ("W_off", C.c_int64), ("P_off", C.c_int64),
                 ("key_off", C.c_int64), ("idx_off", C.c_int64), ("wt_off", C.c_int64),
                 ("col_off", C.c_int64), ("total_bytes", C.c_int64)]
 

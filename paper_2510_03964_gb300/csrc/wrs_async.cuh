@@ -72,9 +72,9 @@ static __device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t pa
 }
 
 // Byte offsets of one stage's planes in shared memory (tile of T pixels).
-// cs = 2 (FP16 colour: K weight planes, then K planes of 8-byte half records
-// {r, g, b, 0}) or 4 (FP32 colour: K float4 {w, r, g, b} record planes,
-// starting at `col`; `wt` == `col`).
+// cs = 2 (FP16 colour: K planes of the weights' low 16 bits, then K planes of
+// 8-byte records {r, g, b, w_hi}) or 4 (FP32 colour: K float4 {w, r, g, b}
+// record planes, starting at `col`; `wt` == `col`).
 struct StageLayout {
   uint32_t frame, W, P, key, wt, col, bytes;
 };
@@ -87,7 +87,7 @@ __host__ __device__ __forceinline__ StageLayout stage_layout(int T, int K, int c
   L.key = L.P + 4u * T;
   if (cs == 2) {
     L.wt = L.key + 4u * K * T;
-    L.col = L.wt + (resolve ? 4u * K * T : 0u);
+    L.col = L.wt + (resolve ? 2u * K * T : 0u);
     L.bytes = L.col + (resolve ? 8u * K * T : 0u);
   } else {
     L.wt = L.col = L.key + 4u * K * T;
@@ -117,7 +117,7 @@ __device__ __forceinline__ void issue_tile_copies(const StreamDev& s, const Fram
   if (lane == 0) {
     uint32_t bytes = (copy_frame ? 12u * np : 0u) + 8u * n + 4u * K * n;
     if (skip) bytes -= 4u * n + 4u * K * n;
-    if (resolve) bytes += cs == 2 ? (4u * K * n + 8u * K * n) : 16u * K * n;
+    if (resolve) bytes += cs == 2 ? (2u * K * n + 8u * K * n) : 16u * K * n;
     mbar_arrive_expect_tx(bar, bytes + extra_tx);
   }
   __syncwarp();
@@ -140,7 +140,7 @@ __device__ __forceinline__ void issue_tile_copies(const StreamDev& s, const Fram
                static_cast<const float4*>(s.col) + j * pl + p0, 16u * n, bar);
     } else if (c < 3 + 2 * K) {
       const int j = c - 3 - K;
-      bulk_g2s(stage + L.wt + 4u * T * j, s.wt + j * pl + p0, 4u * n, bar);
+      bulk_g2s(stage + L.wt + 2u * T * j, s.wt + j * pl + p0, 2u * n, bar);
     } else {
       const int j = c - 3 - 2 * K;  // FP16 colour: record plane j
       bulk_g2s(stage + L.col + 8u * T * j, static_cast<const uint2*>(s.col) + j * pl + p0,
@@ -180,7 +180,7 @@ __device__ __forceinline__ int compute_tile(const StreamDev& s, const FrameDev& 
   src.W = reinterpret_cast<const float*>(st + L.W);
   src.P = reinterpret_cast<const float*>(st + L.P);
   src.key = reinterpret_cast<const float*>(st + L.key);
-  src.wt = reinterpret_cast<const float*>(st + L.wt);
+  src.wt = reinterpret_cast<const uint16_t*>(st + L.wt);
   src.col = st + L.col;
   src.stride = T;
   src.at = tl;

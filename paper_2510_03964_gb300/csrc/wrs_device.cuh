@@ -138,10 +138,11 @@ struct StreamDev {
   float* P;          // [plane]
   float* key;        // [K][plane]
   uint32_t* idx;     // [K][plane]
-  float* wt;         // FP16 colour: [K][plane] slot weights; FP32 colour: unused
+  uint16_t* wt;      // FP16 colour: [K][plane] low 16 bits of the slot weights; FP32: unused
   void* col;         // FP32 colour: [K][plane] float4 records {w, r, g, b} (weight and colour
                      // of a slot in one 16-byte entry); FP16 colour: [K][plane] 8-byte
-                     // records {r, g, b, 0} of halves
+                     // records {r, g, b, w_hi}: the colour as IEEE halves and the high 16
+                     // bits of the slot weight (with `wt`, the FP32 weight bit for bit)
   int64_t plane;     // entries per plane (multiple of 64)
   int32_t width, height, K, hw;
   uint32_t width_rcp; // ceil(2^32 / width) (0xFFFFFFFF for width 1): see row_of
@@ -248,20 +249,29 @@ __device__ __forceinline__ void store_f(float* p, const float (&v)[N]) {
   *reinterpret_cast<typename VecF<N>::T*>(p) = t;
 }
 
+// FP16 colour: a slot's FP32 weight from the high half stored in its record's
+// fourth half word (rec_hi = the record's second 32-bit word) and the low half
+// from the weight plane.
+__device__ __forceinline__ float slot_weight_f16(uint32_t rec_hi, uint32_t lo) {
+  return __uint_as_float((rec_hi & 0xffff0000u) | (lo & 0xffffu));
+}
+
 // Weight and colour of slot j for a group of N pixels whose first entry is at
 // `at` in planes of `stride` entries. FP32 colour: one float4 record
-// {w, r, g, b} per entry in `col`; FP16 colour: a weight plane and an 8-byte
-// record {r, g, b, 0} of halves per entry in `col`.
+// {w, r, g, b} per entry in `col`; FP16 colour: an 8-byte record
+// {r, g, b, w_hi} per entry in `col` (colour as halves) and the low 16 bits of
+// the weight in the uint16 plane `wt`.
 template <bool F16, int N>
-__device__ __forceinline__ void load_slot(const float* wt, const void* col, int K, int j,
+__device__ __forceinline__ void load_slot(const uint16_t* wt, const void* col, int K, int j,
                                           int64_t stride, int64_t at, float (&a)[N],
                                           float (&r)[N], float (&g)[N], float (&b)[N]) {
   if constexpr (F16) {
-    load_f<N>(wt + j * stride + at, a);
+    const uint16_t* lo = wt + j * stride + at;
     const uint2* rec = static_cast<const uint2*>(col) + j * stride + at;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       const uint2 v = rec[i];
+      a[i] = slot_weight_f16(v.y, lo[i]);
       r[i] = __half2float(__ushort_as_half(static_cast<unsigned short>(v.x & 0xffffu)));
       g[i] = __half2float(__ushort_as_half(static_cast<unsigned short>(v.x >> 16)));
       b[i] = __half2float(__ushort_as_half(static_cast<unsigned short>(v.y & 0xffffu)));
@@ -281,14 +291,15 @@ __device__ __forceinline__ void load_slot(const float* wt, const void* col, int 
 
 // Writes slot j of pixel p (global planes of `plane` entries).
 template <bool F16>
-__device__ __forceinline__ void store_slot(float* wt, void* col, int K, int j, int64_t plane,
+__device__ __forceinline__ void store_slot(uint16_t* wt, void* col, int K, int j, int64_t plane,
                                            int64_t p, float w, float r, float g, float b) {
   if constexpr (F16) {
-    wt[j * plane + p] = w;
+    const uint32_t wb = __float_as_uint(w);
+    wt[j * plane + p] = static_cast<uint16_t>(wb & 0xffffu);
     const uint32_t rb = __half_as_ushort(__float2half_rn(r));
     const uint32_t gb = __half_as_ushort(__float2half_rn(g));
     const uint32_t bb = __half_as_ushort(__float2half_rn(b));
-    static_cast<uint2*>(col)[j * plane + p] = make_uint2(rb | (gb << 16), bb);
+    static_cast<uint2*>(col)[j * plane + p] = make_uint2(rb | (gb << 16), bb | (wb & 0xffff0000u));
   } else {
     static_cast<float4*>(col)[j * plane + p] = make_float4(w, r, g, b);
   }
@@ -338,7 +349,7 @@ struct Src {
   const float* W;
   const float* P;
   const float* key;
-  const float* wt;
+  const uint16_t* wt;
   const void* col;
   int64_t stride;
   int64_t at;

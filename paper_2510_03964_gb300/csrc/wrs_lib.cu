@@ -75,14 +75,16 @@ void wrs_make_layout(const wrs_config* c, wrs_layout* L) {
   L->plane_px = pl;
   L->plane_bytes4 = pl * 4;
   L->plane_bytes_col = pl * (c->color_fp16 ? 8 : 16);
+  L->plane_bytes_wt = c->color_fp16 ? pl * 2 : 0;
   L->status_off = 0;
   L->W_off = kStatusBytes;
   L->P_off = L->W_off + L->plane_bytes4;
   L->key_off = L->P_off + L->plane_bytes4;
   L->idx_off = L->key_off + c->K * L->plane_bytes4;
   if (c->color_fp16) {
+    // low halves of the slot weights (uint16), then 8-byte records {r, g, b, w_hi}
     L->wt_off = L->idx_off + c->K * L->plane_bytes4;
-    L->col_off = L->wt_off + c->K * L->plane_bytes4;
+    L->col_off = (L->wt_off + c->K * L->plane_bytes_wt + 255) / 256 * 256;
     L->total_bytes = L->col_off + c->K * L->plane_bytes_col;
   } else {
     // FP32 colour: weight and colour of a slot in one float4 record
@@ -104,7 +106,7 @@ StreamDev wrs_stream_dev(const wrs_ctx* x) {
   s.P = reinterpret_cast<float*>(b + x->lay.P_off);
   s.key = reinterpret_cast<float*>(b + x->lay.key_off);
   s.idx = reinterpret_cast<uint32_t*>(b + x->lay.idx_off);
-  s.wt = x->lay.wt_off >= 0 ? reinterpret_cast<float*>(b + x->lay.wt_off) : nullptr;
+  s.wt = x->lay.wt_off >= 0 ? reinterpret_cast<uint16_t*>(b + x->lay.wt_off) : nullptr;
   s.col = b + x->lay.col_off;
   s.plane = x->lay.plane_px;
   s.width = x->cfg.width;
@@ -168,7 +170,7 @@ __global__ void init_kernel(StreamDev s) {
     for (int j = 0; j < s.K; ++j) {
       s.key[j * n + i] = wrs::kInf;
       s.idx[j * n + i] = wrs::kEmpty;
-      if (s.wt) s.wt[j * n + i] = 0.0f;  // FP32 records are zeroed with the colour region
+      if (s.wt) s.wt[j * n + i] = 0;  // records are zeroed with the colour region
     }
   }
 }

@@ -75,7 +75,8 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // Shared staging of one block's gathered histories, one column per thread:
 // W, P, key[KT], idx[KT], then (FP32 colour) KT float4 records {w, r, g, b}
-// or (FP16 colour) KT weights and KT 8-byte half records.
+// or (FP16 colour) KT words of the weight-low plane (the aligned pair of
+// entries holding the source pixel's) and KT 8-byte records {r, g, b, w_hi}.
 template <int KT, bool F16>
 struct Hist {
   static constexpr int kW = 0;
@@ -108,7 +109,7 @@ __device__ __forceinline__ int reproject_keys(const StreamDev& cur, const Stream
   float* sP = reinterpret_cast<float*>(smem + H::kP) + tid;
   float* sKey = reinterpret_cast<float*>(smem + H::kKey) + tid;
   uint32_t* sIdx = reinterpret_cast<uint32_t*>(smem + H::kIdx) + tid;
-  float* sWt = reinterpret_cast<float*>(smem + H::kWt) + tid;
+  uint32_t* sWt = reinterpret_cast<uint32_t*>(smem + H::kWt) + tid;
   uint8_t* sRec = smem + H::kRec + (F16 ? 8 : 16) * tid;
   constexpr int kRecStride = (F16 ? 8 : 16) * kThreads;
 
@@ -123,7 +124,8 @@ __device__ __forceinline__ int reproject_keys(const StreamDev& cur, const Stream
     cp_async4(sKey + j * kThreads, prev.key + j * pl + q);
     cp_async4(sIdx + j * kThreads, prev.idx + j * pl + q);
     if constexpr (F16) {
-      cp_async4(sWt + j * kThreads, prev.wt + j * pl + q);
+      // 2-byte entries: copy the 4-byte pair holding q's (in the plane: its length is even)
+      cp_async4(sWt + j * kThreads, prev.wt + j * pl + (q & ~static_cast<int64_t>(1)));
       cp_async8(sRec + j * kRecStride, static_cast<const uint2*>(prev.col) + j * pl + q);
     } else {
       cp_async16(sRec + j * kRecStride, static_cast<const float4*>(prev.col) + j * pl + q);
@@ -141,10 +143,11 @@ __device__ __forceinline__ int reproject_keys(const StreamDev& cur, const Stream
   cp_async_wait_all();
 
   // slot j of the gathered history, from this thread's column
+  const int lo_shift = 16 * static_cast<int>(q & 1);  // q's half of each weight-low pair
   auto slot = [&](int j, float& a, float& cr, float& cg, float& cb) {
     if constexpr (F16) {
-      a = sWt[j * kThreads];
       const uint2 v = *reinterpret_cast<const uint2*>(sRec + j * kRecStride);
+      a = slot_weight_f16(v.y, sWt[j * kThreads] >> lo_shift);
       cr = __half2float(__ushort_as_half(static_cast<unsigned short>(v.x & 0xffffu)));
       cg = __half2float(__ushort_as_half(static_cast<unsigned short>(v.x >> 16)));
       cb = __half2float(__ushort_as_half(static_cast<unsigned short>(v.y & 0xffffu)));
@@ -221,8 +224,8 @@ __device__ __forceinline__ int reproject_keys(const StreamDev& cur, const Stream
       cur.key[j * pl + p] = kj;
       cur.idx[j * pl + p] = sIdx[j * kThreads];
       if constexpr (F16) {
-        // the half record moves unchanged; its weight beside it
-        cur.wt[j * pl + p] = sWt[j * kThreads];
+        // the record moves unchanged; the low half of its weight beside it
+        cur.wt[j * pl + p] = static_cast<uint16_t>(sWt[j * kThreads] >> lo_shift);
         static_cast<uint2*>(cur.col)[j * pl + p] =
             *reinterpret_cast<const uint2*>(sRec + j * kRecStride);
       } else {

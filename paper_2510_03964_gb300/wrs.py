@@ -261,10 +261,13 @@ def unpack_state(buf: np.ndarray, lay: WrsLayout, K: int, hw: int, color_fp16: b
         "idx": plane(lay.idx_off, np.uint32, K).copy(),
     }
     if color_fp16:
-        out["wt"] = plane(lay.wt_off, np.float32, K).copy()
-        rec = np.frombuffer(buf, dtype=np.float16, count=K * pl * 4, offset=lay.col_off)
+        # the weight's low 16 bits in their own plane, its high 16 bits in the
+        # record's fourth half word
+        lo = plane(lay.wt_off, np.uint16, K).astype(np.uint32)
+        rec = np.frombuffer(buf, dtype=np.uint16, count=K * pl * 4, offset=lay.col_off)
         rec = rec.reshape(K, pl, 4)[:, :hw]
-        out["col"] = np.ascontiguousarray(np.transpose(rec[:, :, :3], (2, 0, 1)))
+        out["wt"] = ((rec[:, :, 3].astype(np.uint32) << 16) | lo).view(np.float32)
+        out["col"] = np.ascontiguousarray(np.transpose(rec[:, :, :3].view(np.float16), (2, 0, 1)))
     else:
         rec = np.frombuffer(buf, dtype=np.float32, count=K * pl * 4, offset=lay.col_off)
         rec = rec.reshape(K, pl, 4)[:, :hw]

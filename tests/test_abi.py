@@ -45,9 +45,14 @@ def test_state_bytes_and_layout(lib):
         assert off % 256 == 0
     cfg16 = pkg.make_config(3840, 2160, 8, 200.0, color_fp16=True)
     lay16 = pkg.state_layout(cfg16)
-    # FP16 colour: W, P, key[8], idx[8], wt[8] float planes + 8 records of 4 halves
-    assert pkg.state_bytes(cfg16) == 256 + pl * (4 * (2 + 3 * 8) + 8 * 8)
-    assert lay16.wt_off > 0 and lay16.plane_bytes_col == 8 * pl
+    # FP16 colour: W, P, key[8], idx[8] float planes, 8 uint16 planes of the
+    # weights' low halves, 8 records {r, g, b, w_hi} of 4 halves
+    assert pkg.state_bytes(cfg16) == 256 + pl * (4 * (2 + 2 * 8) + 2 * 8 + 8 * 8)
+    assert lay16.wt_off > 0 and lay16.plane_bytes_col == 8 * pl and lay16.plane_bytes_wt == 2 * pl
+    assert lay16.col_off % 256 == 0 and lay.plane_bytes_wt == 0
+    # odd K: the weight planes end off a 256-byte boundary and the records start on the next
+    lay3 = pkg.state_layout(pkg.make_config(8, 8, 3, 2.0, color_fp16=True))
+    assert lay3.col_off == (lay3.wt_off + 3 * 2 * lay3.plane_px + 255) // 256 * 256
     # ragged size: planes padded to 64 entries
     lay2 = pkg.state_layout(pkg.make_config(37, 23, 3, 5.0))
     assert lay2.plane_px == 896
