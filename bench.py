@@ -7,8 +7,9 @@ pushed cyclically. One step = one frame pushed through the whole per-pixel
 path (weight, key, temporal bias, K-slot combine, resolve) = one kernel
 launch. The stream first runs one untimed pass of its 240 frames (reported
 as ``first_pass``), so the timed frames sit at the same age of the stream
-whatever --steps and --warmup are. The state (1.9 GB per frame touched) is far larger than the 129 MB
-L2, so no flush is needed between steps.
+whatever --steps and --warmup are. The state (1.66 GB, all of it touched
+every frame) is far larger than the 129 MB L2, so no flush is needed
+between steps.
 
 Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle
 instead (the method has no reference GPU implementation).
@@ -583,7 +584,7 @@ def run_reprojection(args, dev):
                          "kernel": "reproject_kernel<fp32>"},
             "loop_mip_foveate_reproject_ms_per_frame": round(a.elapsed_time(b) / args.reproj_steps, 4),
             "note": "the frames' images, motion and depth are rendered on the device before the "
-                    "timed region; inputs (1.9 GB of state per buffer) exceed L2"}
+                    "timed region; inputs (1.66 GB of state per buffer) exceed L2"}
 
 
 def run_serving(args, dev):
