@@ -844,7 +844,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="4k",
-                    choices=["4k", "4k_fp16", "hd", "hd_k8", "tiny", "4k_k1", "4k_k1_literal", "4k_bias2"])
+                    choices=["4k", "4k_fp16", "hd", "hd_k8", "hd_k8_fp16", "tiny", "4k_k1", "4k_k1_literal",
+                             "4k_bias2"])
     ap.add_argument("--age", type=int, default=-1,
                     help="untimed frames pushed before the warm-up (default: one pass of the "
                          "workload's frame sequence)")

@@ -243,9 +243,11 @@ int wrs_get_launch(const wrs_ctx* ctx, int* block_threads, int* px_per_thread);
  * frame/out are 16-byte aligned (else the plain kernel runs): persistent CTAs
  * (ctas_per_sm per SM; 0 = as many as registers and shared memory allow)
  * stream tiles of 256 * px_per_thread pixels (1, 2 or 4) through `stages`
- * shared-memory stages with bulk asynchronous copies. 0 for px_per_thread /
- * stages selects 256-pixel tiles and two stages. Results are bit-identical
- * across every choice. WRS_ERR_ARG if the stages do not fit in shared memory. */
+ * shared-memory stages with bulk asynchronous copies. 0 for px_per_thread
+ * selects 256-pixel tiles; 0 for stages selects as many stages (up to four)
+ * as keep two CTAs on an SM, else as many as one CTA holds (the default for
+ * a new context). Results are bit-identical across every choice. WRS_ERR_ARG
+ * if the stages do not fit in shared memory. */
 int wrs_set_pipeline(wrs_ctx* ctx, int enable, int px_per_thread, int stages, int ctas_per_sm);
 int wrs_get_pipeline(const wrs_ctx* ctx, int* enable, int* px_per_thread, int* stages,
                      int* ctas_per_sm);

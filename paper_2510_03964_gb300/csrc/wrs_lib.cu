@@ -131,13 +131,22 @@ uint32_t* wrs_status_word(const wrs_ctx* x) {
   return reinterpret_cast<uint32_t*>(x->state + x->lay.status_off);
 }
 
+// Stages of `px` pixels per thread: as many (up to four) as keep two CTAs on
+// an SM, else what one CTA holds. More stages keep more bytes in flight; the
+// kernels wait on copies, not on arithmetic.
+static int wrs_default_stages(int K, bool f16, int px) {
+  constexpr size_t kSmPerSm = 228 * 1024, kReservedPerCta = 1024;
+  int st = 4;
+  while (st > 2 && 2 * (wrs_pipe_smem_bytes(K, f16, px, st, true) + kReservedPerCta) > kSmPerSm) --st;
+  while (st > 1 && wrs_pipe_smem_bytes(K, f16, px, st, true) > kSmemBudget) --st;
+  return st;
+}
+
 void wrs_default_pipe(int K, bool f16, int* px, int* stages) {
-  // 256-pixel tiles, two stages (several CTAs per SM where they fit); three or
-  // four stages when one CTA's two stages would leave shared memory unused
+  // 256-pixel tiles with the stages above: K = 8 FP32 gets two stages at two
+  // CTAs per SM, K = 8 FP16 three, K <= 4 four
   *px = 1;
-  int st = 2;
-  while (st > 1 && wrs_pipe_smem_bytes(K, f16, 1, st, true) > kSmemBudget) --st;
-  *stages = st;
+  *stages = wrs_default_stages(K, f16, 1);
 }
 
 extern "C" size_t wrs_state_bytes(const wrs_config* cfg) {
@@ -554,11 +563,7 @@ extern "C" int wrs_set_pipeline(wrs_ctx* x, int enable, int px_per_thread, int s
   if (px_per_thread == 0) px_per_thread = dpx;
   if (px_per_thread != 1 && px_per_thread != 2 && px_per_thread != 4)
     return wrs_fail(WRS_ERR_ARG, "px_per_thread must be 1, 2 or 4");
-  if (stages == 0) {
-    stages = 2;
-    while (stages > 1 && wrs_pipe_smem_bytes(x->cfg.K, f16, px_per_thread, stages, true) > kSmemBudget)
-      --stages;
-  }
+  if (stages == 0) stages = wrs_default_stages(x->cfg.K, f16, px_per_thread);
   if (stages < 1 || stages > 8) return wrs_fail(WRS_ERR_ARG, "stages must be in 1..8");
   if (ctas_per_sm < 0 || ctas_per_sm > 8) return wrs_fail(WRS_ERR_ARG, "ctas_per_sm must be in 0..8");
   const size_t need = wrs_pipe_smem_bytes(x->cfg.K, f16, px_per_thread, stages, true);

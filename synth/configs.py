@@ -89,6 +89,9 @@ WORKLOADS = {
         "hd_k8", "1920x1080 RGB FP32, 120 frames, K=8, fovea 120 px, rings as hd: the 4k slot "
         "layout at a quarter of the pixels (profiling case)",
         (StreamSpec(1920, 1080, 8, _RINGS_HD, seed=0, frames=120),)),
+    "hd_k8_fp16": Workload(
+        "hd_k8_fp16", "as hd_k8 with FP16 colour planes (profiling case)",
+        (StreamSpec(1920, 1080, 8, _RINGS_HD, seed=0, frames=120, color_fp16=True),)),
     "4k_k1": Workload(
         "4k_k1", "as 4k with one slot (n = 1, the paper's reservoir), exponential-key race",
         (StreamSpec(3840, 2160, 1, _RINGS_4K, seed=0, frames=240),)),

@@ -87,6 +87,18 @@ def test_pipeline_rejects_oversized_stages():
     st.close()
 
 
+@pytest.mark.parametrize("K,fp16,stages", [(8, False, 2), (8, True, 3), (4, False, 4), (4, True, 4),
+                                            (16, False, 2)])
+def test_default_stages_keep_two_ctas_per_sm(K, fp16, stages):
+    # as many stages (up to four) as keep two CTAs on an SM, else what one CTA holds
+    import paper_2510_03964_gb300 as wrs
+    st = wrs.Stream(64, 16, K, 8.0, color_fp16=fp16, device=torch.device("cuda"))
+    assert st.get_pipeline() == (True, 1, stages, 0)
+    st.set_pipeline(True, 0, 0)
+    assert st.get_pipeline() == (True, 1, stages, 0)
+    st.close()
+
+
 def test_pipeline_many_tiles_per_cta():
     """More tiles than CTAs: every CTA walks several tiles through its stages."""
     run = PairedRun(640, 480, 4, r_f=40.0, frames=6, seed=8, jitter_px=60, pipeline=(True, 2, 3, 0),
