@@ -614,12 +614,22 @@ def workload_config(spec, name):
             "parallelism": "replicas (one independent stream per GPU)"}
 
 
-def run_ours(args, world, rank, local):
+# The stream age the timed frames sit at: a stream's replacement rate (and so
+# the cost of a frame) falls as the stream ages, so every timed frame is taken
+# from the same window of ages whatever --steps is. The stream first runs one
+# pass of the workload's frame sequence (frames 0..239); its state there is
+# exported once, and every block of WINDOW timed frames starts from that state
+# again (wrs_import_state, outside the timed events), pushing frames of ages
+# WINDOW_AGE .. WINDOW_AGE + WINDOW - 1.
+WINDOW = 20
+
+
+def measure_stream(args, dev, spec, seed, world, clocks_rank0: bool, steps: int, warmup: int,
+                   want_clocks: bool = True) -> dict:
+    """One stream of `spec` on `dev`: its first pass (frames 0..frames-1, timed
+    per frame) and then `warmup` + `steps` pushes from the fixed age window.
+    Returns the per-step kernel times and the counts behind the roofline."""
     import paper_2510_03964_gb300 as wrs
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    spec = workload(args.workload).streams[0]
-    seed = spec.seed + rank
     fv = Foveator(spec.width, spec.height, spec.radii, seed=seed, device=dev)
     gaze = gaze_path(spec.width, spec.height, spec.frames, seed=seed, model=spec.gaze_model,
                      jitter_px=spec.jitter_px)
@@ -642,58 +652,150 @@ def run_ours(args, world, rank, local):
     def push(t):
         st.push_frame(frames[t % nfr], gaze[t % nfr], None, out, stream=stream)
 
-    # The stream's age sets its replacement rate (every pixel inserts in the
-    # first K frames, then the rate falls as the history's weight grows), so
-    # the stream first runs one untimed pass of the workload's frame sequence:
-    # the timed frames then sit at the same point of a running stream whatever
-    # --steps and --warmup are. That pass is timed on its own as the cost of a
-    # fresh stream's first frames.
+    # first pass: a fresh stream's frames 0 .. age-1, each timed on its own
     age = spec.frames if args.age < 0 else args.age
     first_pass = None
     if age > 0:
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(age)]
         r0 = st.replacements(stream=stream)
         with torch.cuda.stream(stream):
-            a0.record(stream)
             for t in range(age):
+                ev[t][0].record(stream)
                 push(t)
-            a1.record(stream)
+                ev[t][1].record(stream)
         torch.cuda.synchronize()
-        first_pass = {"frames": age, "ms_per_frame": round(a0.elapsed_time(a1) / age, 4),
+        ft = [a.elapsed_time(b) for a, b in ev]
+        rest = ft[1:] if len(ft) > 1 else ft
+        first_pass = {"frames": age, "ms_per_frame_1_to_end": round(statistics.mean(rest), 4),
+                      "frame0_ms": round(ft[0], 4),
                       "replacement_rate": round((st.replacements(stream=stream) - r0) / float(hw * age), 4),
-                      "note": "a fresh stream's first frames, pushed back to back before the warm-up "
-                              "(untimed for value)"}
-    with torch.cuda.stream(stream):
-        for t in range(args.warmup):
-            push(age + t)
-    torch.cuda.synchronize()
+                      "note": f"a fresh stream's frames 0..{age - 1} pushed back to back (the workload's "
+                              f"own {spec.frames}-frame sequence); ms_per_frame_1_to_end is the mean "
+                              f"kernel time of frames 1..{age - 1}, frame 0 (all inserts, first "
+                              f"launch) reported apart"}
+    # the state at the window's start, kept in pinned host memory
+    snap = torch.empty(st.nbytes, dtype=torch.uint8, pin_memory=True)
+    lib = wrs.load()
+    from paper_2510_03964_gb300._lib import check
+    check(lib.wrs_export_state(st._ctx, snap.data_ptr(), st.nbytes, stream.cuda_stream))
 
-    clocks = ClockSampler(local) if rank == 0 else None
+    def run(n, timed):
+        times, repl = [], 0
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(min(n, WINDOW))]
+        i = 0
+        while i < n:
+            check(lib.wrs_import_state(st._ctx, snap.data_ptr(), st.nbytes, age, stream.cuda_stream))
+            r0 = st.replacements(stream=stream)
+            m = min(WINDOW, n - i)
+            with torch.cuda.stream(stream):
+                for k in range(m):
+                    if timed:
+                        evs[k][0].record(stream)
+                    push(age + k)
+                    if timed:
+                        evs[k][1].record(stream)
+            torch.cuda.synchronize()
+            repl += st.replacements(stream=stream) - r0
+            if timed:
+                times += [evs[k][0].elapsed_time(evs[k][1]) for k in range(m)]
+            i += m
+        return times, repl
+
+    run(warmup, False)
+    clocks = ClockSampler(dev.index or 0) if (clocks_rank0 and want_clocks) else None
     time.sleep(0.3 if clocks else 0.0)
-    repl0 = st.replacements(stream=stream)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier(world)
     torch.cuda.synchronize()
-    with torch.cuda.stream(stream):
-        for i in range(args.steps):
-            starts[i].record(stream)
-            push(age + args.warmup + i)
-            ends[i].record(stream)
+    kernel_ms, repl = run(steps, True)
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop() if clocks else None
-    rho = (st.replacements(stream=stream) - repl0) / float(hw * args.steps)
-    total_ms = starts[0].elapsed_time(ends[-1])
-    kernel_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = max_over_ranks(world, total_ms, dev)
+    res = {"kernel_ms": kernel_ms, "rho": repl / float(hw * steps), "first_pass": first_pass,
+           "clocks": clk, "age": age, "stream": st, "frames": frames, "gaze": gaze, "fv": fv,
+           "out": out, "cuda_stream": stream, "nfr": nfr}
+    return res
+
+
+def roofline_line(spec, kernel_avg_ms, rho, peaks, workload_name, kname):
+    lit = spec.update_rule == 1
+    hw = spec.width * spec.height
+    bpp = (algorithmic_bytes_per_px(spec.K, spec.color_fp16, lit)
+           + rho * replacement_bytes(spec.color_fp16, lit))
+    achieved = bpp * hw / (kernel_avg_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+            "traffic": recorded_traffic(kname, workload_name),
+            "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs, copy)",
+            "algorithmic_bytes_per_px": round(bpp, 2),
+            "bytes_rule": f"{algorithmic_bytes_per_px(spec.K, spec.color_fp16, lit)} B read/written "
+                          f"by every pixel-update + replacement rate {rho:.4f} (counted on the "
+                          f"device over the timed frames) x {replacement_bytes(spec.color_fp16, lit)} B",
+            "kernel": kname}
+
+
+def kernel_name(st, spec):
+    st_pipe = st.get_pipeline()
+    return (f"{'pipe_kernel' if st_pipe[0] else 'push_kernel'}"
+            f"<K={spec.K},{'fp16' if spec.color_fp16 else 'fp32'}>")
+
+
+def resolve_error_leg(args, dev, spec, seed, m):
+    """The oracle on the host cores over the workload's frames at sampled
+    pixels, and a fresh GPU stream fed the same frames: the oracle's time per
+    frame and the GPU's resolve error against the oracle's FP64 resolve."""
+    import paper_2510_03964_gb300 as wrs
+    nthreads = os.cpu_count() or 1
+    pixels = sample_pixels(spec, args.cpu_sample)
+    stream = m["cuda_stream"]
+    st_err = wrs.Stream(spec.width, spec.height, spec.K, spec.r_f, seed=seed,
+                        stream_id=spec.stream_id, color_fp16=spec.color_fp16,
+                        temporal_bias=spec.temporal_bias, device=dev, stream=stream,
+                        update_rule=spec.update_rule)
+    buf = torch.empty((spec.height, spec.width, 3), dtype=torch.float32, device=dev)
+    out = m["out"]
+    pix_d = torch.as_tensor(pixels, device=dev)
+    fv = m["fv"]
+
+    def gpu_out(t, g):
+        with torch.cuda.stream(stream):
+            fv.frame(float(g[0]), float(g[1]), out=buf)
+            st_err.push_frame(buf, g, None, out, stream=stream)
+            sel = out.view(-1, 3)[pix_d].double()
+        torch.cuda.synchronize()
+        return sel.cpu().numpy()
+
+    ms_cpu, n_frames, err = oracle_ms_per_frame(spec, pixels, spec.frames, nthreads, fv, m["gaze"],
+                                                budget_s=args.cpu_budget_s, gpu_out=gpu_out)
+    st_err.close()
+    hw = spec.width * spec.height
+    base = {"value": round(ms_cpu, 3), "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"{len(pixels)} of {hw} pixels (every {hw // len(pixels)}th), {n_frames} frames, "
+                      f"mean of frames 1.. scaled to a full frame; oracle threads over pixels"}
+    return base, err
+
+
+def run_ours(args, world, rank, local):
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    spec = workload(args.workload).streams[0]
+    seed = spec.seed + rank
+    hw = spec.width * spec.height
+    m = measure_stream(args, dev, spec, seed, world, rank == 0, args.steps, args.warmup)
+    st, stream, frames, gaze, out, nfr = (m["stream"], m["cuda_stream"], m["frames"], m["gaze"],
+                                          m["out"], m["nfr"])
+    kernel_ms = m["kernel_ms"]
+    total_ms = max_over_ranks(world, sum(kernel_ms), dev)
     ms_frame = total_ms / (args.steps * world)
     kernel_avg = statistics.mean(kernel_ms)
+    rho = m["rho"]
+    age = m["age"]
 
     # end-to-end through the host-buffer entry point (copies inside the timed region)
     e2e = None
     if args.e2e_steps > 0:
+        import paper_2510_03964_gb300 as wrs
         pool = min(nfr, 8)
         h_frames = torch.empty((pool, spec.height, spec.width, 3), dtype=torch.float32, pin_memory=True)
         for i in range(pool):
@@ -748,30 +850,17 @@ def run_ours(args, world, rank, local):
         return
     st_pipe = st.get_pipeline()
     st_launch = st.get_launch()
-    del frames
-    torch.cuda.empty_cache()
-    batched = run_batched(args, dev) if args.batch_rounds > 0 else None
-    torch.cuda.empty_cache()
-    foveation = run_foveation(args, dev, spec, seed, gaze) if args.fov_reps > 0 else None
-    torch.cuda.empty_cache()
-    reprojection = run_reprojection(args, dev) if args.reproj_steps > 0 else None
-    torch.cuda.empty_cache()
-    serving = run_serving(args, dev) if args.serve > 0 else None
-    torch.cuda.empty_cache()
-
+    kname = kernel_name(st, spec)
     peaks = measured_peaks()
-    lit = spec.update_rule == 1
-    bpp = (algorithmic_bytes_per_px(spec.K, spec.color_fp16, lit)
-           + rho * replacement_bytes(spec.color_fp16, lit))
-    achieved = bpp * hw / (kernel_avg * 1e-3) / 1e9
-    kname = (f"{'pipe_kernel' if st_pipe[0] else 'push_kernel'}"
-             f"<K={spec.K},{'fp16' if spec.color_fp16 else 'fp32'}>")
+    roof = roofline_line(spec, kernel_avg, rho, peaks, args.workload, kname)
     cfg = workload_config(spec, args.workload)
     pipe_on, pipe_px, pipe_st, pipe_ctas = st_pipe
     blk, px = st_launch
     cfg["kernel"] = (f"pipelined: {pipe_px} px/thread, tile {256 * pipe_px} px, {pipe_st} stages, "
                      f"{pipe_ctas or 'max'} CTAs/SM"
                      if pipe_on else f"plain: block {blk}, {px} px/thread")
+    cfg["timed_window"] = (f"stream ages {age}..{age + WINDOW - 1}: the state after the first "
+                           f"{age} frames is restored before every {WINDOW} timed frames")
     if nfr != spec.frames:
         cfg["frames_distinct"] = nfr
     line = {
@@ -782,58 +871,71 @@ def run_ours(args, world, rank, local):
         "mpx_updates_per_s": round(hw * world / (ms_frame * 1e-3) / 1e6, 1),
         "kernel_ms_avg": round(kernel_avg, 4),
         "kernel_ms_median": round(statistics.median(kernel_ms), 4),
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-                     "traffic": recorded_traffic(kname, args.workload),
-                     "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs, copy)",
-                     "algorithmic_bytes_per_px": round(bpp, 2),
-                     "bytes_rule": f"{algorithmic_bytes_per_px(spec.K, spec.color_fp16, lit)} B read/written "
-                                   f"by every pixel-update + replacement rate {rho:.4f} (counted on the "
-                                   f"device over the timed frames) x {replacement_bytes(spec.color_fp16, lit)} B",
-                     "kernel": kname},
+        "roofline": roof,
         "paper": PAPER_CONTEXT,
         "replacement_rate": round(rho, 4),
-        "stream_age_frames": age + args.warmup,
-        "first_pass": first_pass,
-        "pct_nominal_8tbs": round(100 * achieved / 8000.0, 2),
+        "stream_age_frames": f"{age}..{age + WINDOW - 1}",
+        "first_pass": m["first_pass"],
+        "config_240_frame_mean_ms": (m["first_pass"] or {}).get("ms_per_frame_1_to_end"),
+        "pct_nominal_8tbs": round(100 * roof["achieved"] / 8000.0, 2),
         "gpu_launches": args.steps,
-        "clocks": clk,
+        "clocks": m["clocks"],
         "e2e": e2e,
-        "batched": batched,
-        "foveation": foveation,
-        "reprojection": reprojection,
-        "serving": serving,
     }
+    # the precision form (FP16 slot colours) at the same window, beside FP32
+    precision = None
+    m["frames"] = None  # the frames of this workload are no longer needed
+    del frames
+    torch.cuda.empty_cache()
+    if args.precision and args.workload == "4k":
+        spec16 = workload("4k_fp16").streams[0]
+        m16 = measure_stream(args, dev, spec16, seed, 1, False, args.precision_steps, args.warmup)
+        k16 = statistics.mean(m16["kernel_ms"])
+        kname16 = kernel_name(m16["stream"], spec16)
+        precision = {
+            "window": cfg["timed_window"], "steps": args.precision_steps,
+            "fp32": {"ms_per_frame": round(kernel_avg, 4), "replacement_rate": round(rho, 4),
+                     "roofline": {"frac": roof["frac"], "achieved": roof["achieved"]}},
+            "fp16": {"ms_per_frame": round(k16, 4), "replacement_rate": round(m16["rho"], 4),
+                     "config_240_frame_mean_ms": (m16["first_pass"] or {}).get("ms_per_frame_1_to_end"),
+                     "roofline": roofline_line(spec16, k16, m16["rho"], peaks, "4k_fp16", kname16)},
+        }
+        if args.cpu_baseline:
+            _, err16 = resolve_error_leg(args, dev, spec16, seed, m16)
+            precision["fp16"]["resolve_error"] = err16
+        m16["stream"].close()
+        del m16
+        torch.cuda.empty_cache()
     if args.cpu_baseline:
+        base, err = resolve_error_leg(args, dev, spec, seed, m)
+        line["resolve_error"] = err
+        # the same oracle on one host thread, on a smaller sample
         nthreads = os.cpu_count() or 1
-        pixels = sample_pixels(spec, args.cpu_sample)
-        # a fresh GPU stream fed the same frames: its resolved colours at the
-        # sampled pixels against the oracle's FP64 resolve (precision per config)
-        st_err = wrs.Stream(spec.width, spec.height, spec.K, spec.r_f, seed=seed,
-                            stream_id=spec.stream_id, color_fp16=spec.color_fp16,
-                            temporal_bias=spec.temporal_bias, device=dev, stream=stream,
-                            update_rule=spec.update_rule)
-        buf = torch.empty((spec.height, spec.width, 3), dtype=torch.float32, device=dev)
-        pix_d = torch.as_tensor(pixels, device=dev)
-
-        def gpu_out(t, g):
-            with torch.cuda.stream(stream):
-                fv.frame(float(g[0]), float(g[1]), out=buf)
-                st_err.push_frame(buf, g, None, out, stream=stream)
-                sel = out.view(-1, 3)[pix_d].double()
-            torch.cuda.synchronize()
-            return sel.cpu().numpy()
-
-        ms_cpu, n_cpu_frames, res_err = oracle_ms_per_frame(
-            spec, pixels, spec.frames, nthreads, fv, gaze, budget_s=args.cpu_budget_s,
-            gpu_out=gpu_out)
-        st_err.close()
-        line["resolve_error"] = res_err
-        line["cpu_baseline"] = {
-            "value": round(ms_cpu, 3), "unit": UNIT, "cores": nthreads, "kind": "oracle",
-            "sample": f"{len(pixels)} of {hw} pixels (every {hw // len(pixels)}th), {n_cpu_frames} frames, "
-                      f"mean of frames 1.. scaled to a full frame; oracle threads over pixels"}
+        small = sample_pixels(spec, args.cpu_sample_single)
+        ms1, n1 = oracle_ms_per_frame(spec, small, spec.frames, 1, m["fv"], gaze,
+                                      budget_s=args.cpu_budget_single_s)
+        base["single_thread"] = {"value": round(ms1, 3), "unit": UNIT, "cores": 1,
+                                 "sample": f"{len(small)} of {hw} pixels, {n1} frames, scaled to a "
+                                           f"full frame"}
+        base["threads"] = nthreads
+        line["cpu_baseline"] = base
+        if precision is not None:
+            precision["fp32"]["resolve_error"] = err
+    line["precision"] = precision
     st.close()
+    torch.cuda.empty_cache()
+    batched = run_batched(args, dev) if args.batch_rounds > 0 else None
+    torch.cuda.empty_cache()
+    foveation = run_foveation(args, dev, spec, seed, gaze) if args.fov_reps > 0 else None
+    torch.cuda.empty_cache()
+    reprojection = run_reprojection(args, dev) if args.reproj_steps > 0 else None
+    torch.cuda.empty_cache()
+    serving = run_serving(args, dev) if args.serve > 0 else None
+    torch.cuda.empty_cache()
+    line["batched"] = batched
+    line["foveation"] = foveation
+    line["reprojection"] = reprojection
+    line["serving"] = serving
     print(json.dumps(line), flush=True)
 
 
@@ -861,6 +963,12 @@ def main():
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--cpu-sample", type=int, default=131072)
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    ap.add_argument("--cpu-sample-single", type=int, default=16384,
+                    help="pixels of the single-threaded oracle timing")
+    ap.add_argument("--cpu-budget-single-s", type=float, default=6.0)
+    ap.add_argument("--precision", type=int, default=1,
+                    help="1: also time the FP16-colour form of the 4k workload at the same window")
+    ap.add_argument("--precision-steps", type=int, default=40)
     ap.add_argument("--ref-sample", type=int, default=65536)
     ap.add_argument("--batch-warmup", type=int, default=240,
                     help="untimed rounds before the timed ones: one pass of the workload's 240 "

@@ -18,7 +18,8 @@
  *  - Status: every int-returning call returns WRS_OK (0) or a WRS_ERR_* code;
  *    wrs_last_error() then holds a one-line message for the calling thread.
  *    A call that fails leaves the reservoir state and the frame counter as
- *    they were.
+ *    they were. Failures found on the device after a call has returned (a
+ *    wait that gave up) are reported by wrs_check_status instead: see there.
  *  - Streams: calls enqueue work on the given CUDA stream (a cudaStream_t
  *    passed as void*; NULL is the legacy default stream) and return without
  *    synchronising, except wrs_export_state / wrs_import_state and
@@ -46,6 +47,8 @@ extern "C" {
 #define WRS_ERR_BUDGET 3   /* state buffer smaller than wrs_state_bytes() */
 #define WRS_ERR_TIMEOUT 4  /* a bounded device-side wait gave up */
 #define WRS_ERR_STATE 5    /* context in the wrong state (e.g. counter exhausted) */
+#define WRS_ERR_CHECK 6    /* checked build only: an index or copy range fell outside its
+                              buffer and was skipped (reported by wrs_check_status) */
 
 #define WRS_MAX_K 16
 #define WRS_MAX_BATCH 64  /* streams in one wrs_push_batch launch */
@@ -99,15 +102,31 @@ typedef struct {
  *                uint16 at wt_off + j*plane_bytes_wt (plane_bytes_wt =
  *                2*plane_px) holds its low 16 bits, so w's bits are
  *                (w_hi << 16) | wlo. col_off is wt_off + K*plane_bytes_wt rounded
- *                up to 256 bytes. */
+ *                up to 256 bytes.
+ * After the planes, a ring of map_frames replacement-code planes of plane_px
+ * bytes (map_off + r*plane_px, r = frame % map_frames): per frame and pixel,
+ * which slot took that frame's sample (0..K-1), 0x80 + j (the history was
+ * flushed, then slot j took the sample) or 0xFF (no change). The update writes this
+ * code, one coalesced byte per pixel, instead of scattering the sample index
+ * into idx[j]; every push also folds the pending codes of one band of
+ * 256-pixel blocks into the idx planes: block b (pixels 256b .. 256b+255) is
+ * folded by the pushes of the frames whose index % map_frames equals its band,
+ * (b + b/16 + b/256) % 16 (integer divisions), which spreads the folding
+ * blocks evenly over the CTAs of the persistent kernels. The idx planes of the other blocks therefore lag by up to
+ * map_frames - 1 frames between pushes; wrs_export_state folds every pending
+ * code first, so exported states always hold complete sample indices, and
+ * the ring is not part of an exported or imported state. */
 typedef struct {
   int64_t plane_px;
   int64_t plane_bytes4;     /* plane_px * 4 */
   int64_t plane_bytes_col;  /* plane_px * 16 (FP32 colour) or * 8 (FP16 colour) */
   int64_t plane_bytes_wt;   /* plane_px * 2 (FP16 colour) or 0 (FP32 colour) */
   int64_t status_off;       /* 256-byte header: uint32 status word (WRS_OK or WRS_ERR_TIMEOUT)
-                               at +0, uint64 count of slot replacements at +8 */
+                               at +0, uint64 count of slot replacements at +8, uint32 check
+                               word of the checked build at +16 */
   int64_t W_off, P_off, key_off, idx_off, wt_off, col_off;
+  int64_t map_off;          /* ring of replacement-code planes (bytes), 256-byte aligned */
+  int64_t map_frames;       /* planes in the ring (a power of two) */
   int64_t total_bytes;
 } wrs_layout;
 
@@ -174,12 +193,18 @@ int wrs_push_frame_host(wrs_ctx* ctx, const float* h_frame, float gaze_x, float 
  * caller still owns the reservoir state buffer. The paper has no counterpart:
  * this only moves frames between host memory and the device. Arguments,
  * results and errors as wrs_push_frame_host, plus WRS_ERR_ARG for frames
- * above WRS_NOALLOC_MAX_PIXELS or another device being current. Allocates no
- * memory. Calls that overlap (from several host threads, or on several CUDA
- * streams of one device, for any stream) share the one staging array and race;
- * serialise them. The first call on a device loads the library's device code
- * and resolves the array's address: make it before any stream capture. The
- * call waits for its copies, as wrs_push_frame_host does. */
+ * above WRS_NOALLOC_MAX_PIXELS or another device being current. The call
+ * itself allocates nothing (no cudaMalloc, no allocating library routine).
+ * The array (207 MB) is device memory all the same: the CUDA runtime backs it
+ * when the library's device code is loaded on a device, which under lazy
+ * module loading (CUDA's default) happens at this entry point's first call on
+ * that device. If the device is then short of memory (a server close to its
+ * budget), that first call fails with WRS_ERR_CUDA: make a warm-up call at
+ * start-up, before memory fills up and before any stream capture. Later calls
+ * reuse the array. Calls that overlap (from several host threads, or on
+ * several CUDA streams of one device, for any stream) share the one staging
+ * array and race; serialise them. The call waits for its copies, as
+ * wrs_push_frame_host does. */
 int wrs_push_frame_host_noalloc(wrs_ctx* ctx, const float* h_frame, float gaze_x, float gaze_y,
                                 const uint8_t* h_fov_map, float* h_out, wrs_stream_t stream);
 
@@ -221,9 +246,14 @@ int wrs_host_pipe_finish(wrs_host_pipe* p);
 /* Finishes, then releases the streams and events (not the stage buffer). */
 int wrs_host_pipe_destroy(wrs_host_pipe* p);
 
-/* Copies the whole state buffer to / from host memory (layout per
- * wrs_state_layout) and waits for the copy. Used for checkpoints, migration
- * of a stream between devices, and tests. Import also sets the frame counter. */
+/* Copies the state (the header and the planes of wrs_state_layout, bytes
+ * 0 .. map_off) to / from host memory and waits for the copy; h_dst / h_src
+ * hold total_bytes, and export writes zeros over the ring's part of h_dst.
+ * Export first folds every pending replacement code into the idx planes (a
+ * kernel on `stream`), so the exported planes are complete. Used for
+ * checkpoints, migration of a stream between devices, and tests. Import also
+ * sets the frame counter and makes a context whose wait gave up usable again
+ * (wrs_check_status). */
 int wrs_export_state(wrs_ctx* ctx, void* h_dst, size_t bytes, wrs_stream_t stream);
 int wrs_import_state(wrs_ctx* ctx, const void* h_src, size_t bytes, uint32_t frame_index,
                      wrs_stream_t stream);
@@ -259,10 +289,24 @@ int wrs_get_pipeline(const wrs_ctx* ctx, int* enable, int* px_per_thread, int* s
  * for tests only (<= 4096). */
 int wrs_set_wait_limit(wrs_ctx* ctx, uint64_t timeout_ns, uint32_t test_extra_tx);
 
-/* Waits for `stream`, reads and clears the status word. WRS_OK, or
- * WRS_ERR_TIMEOUT if a wait gave up since the last check (the frames pushed
- * meanwhile may be partly applied). */
+/* Waits for `stream`, reads and clears the status word (and, in the checked
+ * build, the check word). WRS_OK, WRS_ERR_TIMEOUT if a wait gave up since the
+ * last check, or WRS_ERR_CHECK if the checked build skipped an access outside
+ * its buffer. Either error leaves the reservoirs undefined (the push that
+ * failed was partly applied, and the pipelined kernels leave the state alone
+ * from then until this call): the context is marked failed, and every push,
+ * batch containing it and resolve returns WRS_ERR_STATE until
+ * wrs_import_state restores a saved state (or the context is destroyed and
+ * created again). This is the one exception to "a call that fails leaves the
+ * reservoir state as it was": such failures happen on the device, after the
+ * call that launched the work has returned. */
 int wrs_check_status(wrs_ctx* ctx, wrs_stream_t stream);
+
+/* 1 in the checked build of the library (libwrs_checked.so, compiled with
+ * WRS_CHECKED: every kernel tests the indices and copy ranges it uses against
+ * their buffers, records a failed test in the stream's check word and skips
+ * the access), 0 in the default build. Host only. */
+int wrs_checked_build(void);
 
 /* ------------------------------------------------------------------ batches */
 
@@ -423,7 +467,7 @@ int wrs_push_foveated(wrs_ctx* ctx, const float* d_img, int64_t img_pitch_elems,
                       int32_t filter, float gaze_x, float gaze_y, const uint8_t* d_fov_map,
                       float* d_out, wrs_stream_t stream);
 
-/* Message of the last failed call on this thread ("" if none). *//* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none). */
 const char* wrs_last_error(void);
 
 #ifdef __cplusplus

@@ -8,7 +8,7 @@ import threading
 
 from . import build as _build
 
-WRS_OK, WRS_ERR_ARG, WRS_ERR_CUDA, WRS_ERR_BUDGET, WRS_ERR_TIMEOUT, WRS_ERR_STATE = range(6)
+WRS_OK, WRS_ERR_ARG, WRS_ERR_CUDA, WRS_ERR_BUDGET, WRS_ERR_TIMEOUT, WRS_ERR_STATE, WRS_ERR_CHECK = range(7)
 WRS_MAX_K = 16
 WRS_MAX_BATCH = 64
 WRS_RULE_KEYS, WRS_RULE_LITERAL = 0, 1
@@ -27,7 +27,8 @@ class WrsLayout(C.Structure):
     _fields_ = [("plane_px", C.c_int64), ("plane_bytes4", C.c_int64), ("plane_bytes_col", C.c_int64),
                 ("plane_bytes_wt", C.c_int64), ("status_off", C.c_int64), ("W_off", C.c_int64), ("P_off", C.c_int64),
                 ("key_off", C.c_int64), ("idx_off", C.c_int64), ("wt_off", C.c_int64),
-                ("col_off", C.c_int64), ("total_bytes", C.c_int64)]
+                ("col_off", C.c_int64), ("map_off", C.c_int64), ("map_frames", C.c_int64),
+                ("total_bytes", C.c_int64)]
 
 
 WRS_MAX_MIP_LEVELS = 6
@@ -80,6 +81,7 @@ SIGNATURES = {
     "wrs_host_pipe_push": (_I, [_V, _V, C.c_float, C.c_float, _V, _V]),
     "wrs_host_pipe_finish": (_I, [_V]),
     "wrs_host_pipe_destroy": (_I, [_V]),
+    "wrs_checked_build": (_I, []),
     "wrs_last_error": (C.c_char_p, []),
 }
 
@@ -94,14 +96,20 @@ def header_functions(path: str = HEADER) -> list[str]:
     return sorted(set(re.findall(r"\b(wrs_[a-z0-9_]+)\s*\(", text)))
 
 
+def library_path() -> str:
+    """libwrs.so, or the checked build libwrs_checked.so when the environment
+    sets WRS_CHECKED=1."""
+    return _build.LIB_CHECKED if os.environ.get("WRS_CHECKED") == "1" else _build.LIB
+
+
 def load(build_if_missing: bool = True):
     """Loads libwrs.so (building it first if it is missing or stale)."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
-            if build_if_missing and _build.is_stale():
-                _build.build()
+            path = library_path()
+            if build_if_missing and _build.is_stale(path):
+                _build.build(libs=(path,))
             if not os.path.exists(path):
                 raise RuntimeError(f"libwrs is not built ({path}); run paper_2510_03964_gb300.build.build()")
             lib = C.CDLL(path)

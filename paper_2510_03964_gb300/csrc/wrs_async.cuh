@@ -107,10 +107,29 @@ __device__ __forceinline__ void issue_tile_copies(const StreamDev& s, const Fram
                                                   int cs, bool resolve, const StageLayout& L,
                                                   uint8_t* stage, uint64_t* bar, int64_t p0,
                                                   uint32_t extra_tx, int lane,
-                                                  bool copy_frame = true) {
+                                                  bool copy_frame = true,
+                                                  uint32_t stage_cap = 0xFFFFFFFFu) {
   const int64_t rem_plane = s.plane - p0, rem_px = s.hw - p0;
   const uint32_t n = static_cast<uint32_t>(rem_plane < T ? rem_plane : T);  // plane entries (x64)
   const uint32_t np = static_cast<uint32_t>(rem_px < T ? rem_px : T);       // pixels (x4)
+#ifdef WRS_CHECKED
+  // every copy's global range inside its plane or the frame, and the stage's
+  // layout inside the ring's stage; otherwise no copy is issued and the
+  // barrier completes empty (the consumers then compute stale data, flagged)
+  {
+    bool ok = WRS_IN(s, p0 >= 0 && p0 < s.hw && p0 + n <= s.plane && p0 + np <= s.hw &&
+                            n % 64 == 0 && np % 4 == 0 && K >= 1 && K <= WRS_MAX_K,
+                     kChkCopy);
+    ok = WRS_IN(s, L.bytes <= stage_cap, kChkStageSize) && ok;
+    if (!ok) {
+      if (lane == 0) mbar_arrive_expect_tx(bar, 0u);
+      __syncwarp();
+      return;
+    }
+  }
+#else
+  (void)stage_cap;
+#endif
   // the literal rule (K = 1) reads no P and no key plane: copies 2 and 3 are skipped
   const int skip = s.literal ? 2 : 0;
   const int ncopy = 3 + K + (resolve ? (cs == 2 ? 2 * K : K) : 0);
@@ -172,7 +191,8 @@ __device__ __forceinline__ void draw_tile_uniforms_warp(const StreamDev& s, cons
 template <int KT, bool F16, int PX, int T, bool LIT = false>
 __device__ __forceinline__ int compute_tile(const StreamDev& s, const FrameDev& f,
                                             const StageLayout& L, const uint8_t* st,
-                                            const float* u, int64_t p0, float d_f, int tid) {
+                                            const float* u, int64_t p0, float d_f, int tid,
+                                            const FoldFor<KT>* pre = nullptr) {
   const int tl = tid * PX;
   const int64_t p = p0 + tl;
   if (p >= s.hw) return 0;
@@ -187,12 +207,29 @@ __device__ __forceinline__ int compute_tile(const StreamDev& s, const FrameDev& 
   src.frame = reinterpret_cast<const float*>(st + L.frame) + 3 * tl;
   src.u = u + tl;
   if constexpr (LIT) {
-    if (f.fov != nullptr) return push_group_literal<F16, PX, true, true>(s, f, static_cast<int>(p), src, d_f);
-    return push_group_literal<F16, PX, true, false>(s, f, static_cast<int>(p), src, d_f);
+    if (f.fov != nullptr) return push_group_literal<F16, PX, true, true>(s, f, static_cast<int>(p), src, d_f, pre);
+    return push_group_literal<F16, PX, true, false>(s, f, static_cast<int>(p), src, d_f, pre);
   } else {
-    if (f.fov != nullptr) return push_group<KT, F16, PX, true, true>(s, f, static_cast<int>(p), src, d_f);
-    return push_group<KT, F16, PX, true, false>(s, f, static_cast<int>(p), src, d_f);
+    if (f.fov != nullptr) return push_group<KT, F16, PX, true, true>(s, f, static_cast<int>(p), src, d_f, pre);
+    return push_group<KT, F16, PX, true, false>(s, f, static_cast<int>(p), src, d_f, pre);
   }
+}
+
+// Before a consumer waits for its tile: if the tile's pixel of thread `tid`
+// (one pixel per thread) is in the band this frame folds, load the fold's
+// inputs now, so that their latency passes while the tile is still in flight.
+// Returns whether `in` was filled.
+template <int KM, int PX>
+__device__ __forceinline__ bool prefetch_fold(const StreamDev& s, const FrameDev& f, int64_t p0,
+                                              int tid, FoldIn<KM>& in) {
+  if constexpr (PX == 1) {
+    const int64_t p = p0 + tid;
+    if (s.K <= KM && p < s.hw && folds_now(f, p)) {
+      fold_load(s, s.idx, s.K, f.t, p, in);
+      return true;
+    }
+  }
+  return false;
 }
 
 // Adds a warp's counts to a running total: one atomic per warp.
@@ -203,7 +240,8 @@ template <int KT, bool F16, int PX, int T, bool LIT, int FILTER>
 __device__ __forceinline__ int compute_tile_fov(const StreamDev& s, const FrameDev& f,
                                                 const FovDev& fv, const StageLayout& L,
                                                 uint8_t* st, const float* u, int64_t p0,
-                                                float d_f, int tid) {
+                                                float d_f, int tid,
+                                                const FoldFor<KT>* pre = nullptr) {
   const int tl = tid * PX;
   const int64_t p = p0 + tl;
   if (p >= s.hw) return 0;
@@ -212,7 +250,7 @@ __device__ __forceinline__ int compute_tile_fov(const StreamDev& s, const FrameD
   float* fr = reinterpret_cast<float*>(st + L.frame) + 3 * tl;
 #pragma unroll
   for (int i = 0; i < PX; ++i) fov_pixel<FILTER>(fv, f.gx, f.gy, x + i, y, fr + 3 * i);
-  return compute_tile<KT, F16, PX, T, LIT>(s, f, L, st, u, p0, d_f, tid);
+  return compute_tile<KT, F16, PX, T, LIT>(s, f, L, st, u, p0, d_f, tid, pre);
 }
 
 __device__ __forceinline__ void add_warp_count(unsigned long long* total, int count, int lane) {
@@ -293,13 +331,15 @@ __device__ __forceinline__ int produce(const Ring& r, int my_tiles, uint64_t tim
   return it;
 }
 
-// Consumer warp: for each tile, waits for its stage to land, computes it
+// Consumer warp: for each tile, runs `before_fn(it)` (loads that need not
+// wait for the stage), waits for its stage to land, computes it
 // (`compute_fn(it, stage, u)`), and releases the stage.
-template <typename ComputeFn>
+template <typename BeforeFn, typename ComputeFn>
 __device__ __forceinline__ void consume(const Ring& r, int my_tiles, uint64_t timeout_ns, int lane,
-                                        ComputeFn compute_fn) {
+                                        BeforeFn before_fn, ComputeFn compute_fn) {
   for (int it = 0; it < my_tiles; ++it) {
     const int stg = it % r.S;
+    before_fn(it);
     if (!mbar_wait_bounded(&r.full[stg], (it / r.S) & 1u, timeout_ns)) {
       raise_flag(r);
       break;
@@ -311,8 +351,13 @@ __device__ __forceinline__ void consume(const Ring& r, int my_tiles, uint64_t ti
 }
 
 // After the loops (and a block barrier): if a wait gave up, the producer warp
-// waits (bounded) for the copies of the last S tiles it issued, so that none
-// lands in shared memory after the CTA has exited.
+// waits (bounded) on the full barriers of the last S tiles it issued, giving
+// their copies time to land before the CTA exits. A barrier whose expected
+// bytes can never all arrive (the test_extra_tx fault injection) does not
+// complete even after its copies have landed, so there this wait only spends
+// the limit once per stage: the guarantee then rests on the copies finishing
+// within that time (they take microseconds; the limit is milliseconds), not on
+// observing the barrier.
 __device__ __forceinline__ void drain(const Ring& r, int issued, uint64_t timeout_ns) {
   const int from = issued > r.S ? issued - r.S : 0;
   for (int j = from; j < issued; ++j)

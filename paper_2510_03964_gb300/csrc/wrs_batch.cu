@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ unsigned long long replaced_s[kMaxBatch];  // per stream, this CTA
   __shared__ float d_f_s[kMaxBatch];                    // per stream: density at the fovea edge
+  __shared__ uint32_t failed_s[kMaxBatch];              // per stream: an earlier wait gave up
   constexpr int T = kConsumerWarps * 32 * PX;
   const wrs::Ring r = wrs::make_ring(smem, a.stage_bytes, T, a.stages);
   const int tid = threadIdx.x;
@@ -92,7 +93,12 @@ __global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
   if (tid == 0) wrs::init_ring(r, kConsumerWarps);
   if (tid < kMaxBatch) replaced_s[tid] = 0;
   // each stream's Eq. (phat) normaliser, once per CTA instead of once per tile
-  if (tid < a.n) d_f_s[tid] = wrs::fovea_density(a.e[tid].s);
+  if (tid < a.n) {
+    d_f_s[tid] = wrs::fovea_density(a.e[tid].s);
+    // a stream whose earlier push timed out (not yet seen by the host) has
+    // undefined reservoirs: its tiles are copied but not computed or written
+    failed_s[tid] = *reinterpret_cast<volatile const uint32_t*>(a.e[tid].status);
+  }
   __syncthreads();
 
   const int first = blockIdx.x, step = gridDim.x;
@@ -110,34 +116,45 @@ __global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
                             wrs::draw_tile_uniforms_warp<T>(e.s, e.f, p0, u, ln);
                             __syncwarp();
                             wrs::issue_tile_copies<T>(e.s, e.f, e.s.K, cs, resolve, L, st, full,
-                                                      p0, 0u, ln);
+                                                      p0, 0u, ln, true, r.stage_bytes);
                           });
   } else {
-    wrs::consume(r, my_tiles, a.timeout_ns, lane, [&](int it, const uint8_t* st, const float* u) {
+    // fold inputs of entries that compute with K = 4 or 8 (or the literal
+    // rule), loaded before the wait; the generic-K arithmetic loads its own
+    wrs::FoldIn<8> fin;
+    bool folding = false;
+    wrs::consume(r, my_tiles, a.timeout_ns, lane, [&](int it) {
+      const int g = first + it * step;
+      const BatchEntry& e = a.e[entry_of(a, g)];
+      const int64_t p0 = static_cast<int64_t>(g - e.tile0) * T;
+      folding = (e.code < 4 || e.code > 5) && wrs::prefetch_fold<8, PX>(e.s, e.f, p0, tid, fin);
+    }, [&](int it, const uint8_t* st, const float* u) {
       const int g = first + it * step;
       const int ei = entry_of(a, g);
       const BatchEntry& e = a.e[ei];
       const int64_t p0 = static_cast<int64_t>(g - e.tile0) * T;
       const bool resolve = stage_records(e);
       const float d_f = d_f_s[ei];
+      if (failed_s[ei] != 0) return;
+      const wrs::FoldIn<8>* pre = folding ? &fin : nullptr;
       int rc;
       if constexpr (FAM == kFamF16K48) {
         rc = e.code == 0
-                 ? wrs::compute_tile<4, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 2, resolve), st, u, p0, d_f, tid)
-                 : wrs::compute_tile<8, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 2, resolve), st, u, p0, d_f, tid);
+                 ? wrs::compute_tile<4, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 2, resolve), st, u, p0, d_f, tid, pre)
+                 : wrs::compute_tile<8, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 2, resolve), st, u, p0, d_f, tid, pre);
       } else if constexpr (FAM == kFamF32K48) {
         rc = e.code == 2
-                 ? wrs::compute_tile<4, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 4, resolve), st, u, p0, d_f, tid)
-                 : wrs::compute_tile<8, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 4, resolve), st, u, p0, d_f, tid);
+                 ? wrs::compute_tile<4, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 4, resolve), st, u, p0, d_f, tid, pre)
+                 : wrs::compute_tile<8, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 4, resolve), st, u, p0, d_f, tid, pre);
       } else {
         switch (e.code) {
-        case 0: rc = wrs::compute_tile<4, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 2, resolve), st, u, p0, d_f, tid); break;
-        case 1: rc = wrs::compute_tile<8, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 2, resolve), st, u, p0, d_f, tid); break;
-        case 2: rc = wrs::compute_tile<4, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 4, resolve), st, u, p0, d_f, tid); break;
-        case 3: rc = wrs::compute_tile<8, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 4, resolve), st, u, p0, d_f, tid); break;
+        case 0: rc = wrs::compute_tile<4, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 2, resolve), st, u, p0, d_f, tid, pre); break;
+        case 1: rc = wrs::compute_tile<8, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 2, resolve), st, u, p0, d_f, tid, pre); break;
+        case 2: rc = wrs::compute_tile<4, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 4, resolve), st, u, p0, d_f, tid, pre); break;
+        case 3: rc = wrs::compute_tile<8, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 4, resolve), st, u, p0, d_f, tid, pre); break;
         case 4: rc = wrs::compute_tile<0, true, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 2, resolve), st, u, p0, d_f, tid); break;
-        case 6: rc = wrs::compute_tile<1, true, PX, T, true>(e.s, e.f, wrs::stage_layout(T, 1, 2, resolve), st, u, p0, d_f, tid); break;
-        case 7: rc = wrs::compute_tile<1, false, PX, T, true>(e.s, e.f, wrs::stage_layout(T, 1, 4, resolve), st, u, p0, d_f, tid); break;
+        case 6: rc = wrs::compute_tile<1, true, PX, T, true>(e.s, e.f, wrs::stage_layout(T, 1, 2, resolve), st, u, p0, d_f, tid, pre); break;
+        case 7: rc = wrs::compute_tile<1, false, PX, T, true>(e.s, e.f, wrs::stage_layout(T, 1, 4, resolve), st, u, p0, d_f, tid, pre); break;
         default: rc = wrs::compute_tile<0, false, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 4, resolve), st, u, p0, d_f, tid); break;
         }
       }
@@ -298,6 +315,9 @@ extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
     if (!std::isfinite(gx) || !std::isfinite(gy))
       return wrs_fail(WRS_ERR_ARG, "stream %d: gaze must be finite", i);
     if (x->t == 0xFFFFFFFFu) return wrs_fail(WRS_ERR_STATE, "stream %d: frame counter exhausted", i);
+    if (wrs_require_usable(x) != WRS_OK)
+      return wrs_fail(WRS_ERR_STATE, "stream %d: a device-side wait gave up on it; restore a saved "
+                      "state with wrs_import_state first", i);
     BatchEntry& e = a.e[i];
     e.s = wrs_stream_dev(x);
     e.f.frame = fr;
@@ -307,6 +327,7 @@ extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
     e.f.gx = gx;
     e.f.gy = gy;
     e.f.t = x->t;
+    e.f.map_lo = wrs_map_lo(x);
     e.status = wrs_status_word(x);
     e.tile0 = static_cast<int>(tiles);
     e.code = code_of(x->cfg);

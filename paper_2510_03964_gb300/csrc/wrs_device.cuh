@@ -14,11 +14,15 @@
 #pragma once
 
 #include <cuda_fp16.h>
+#include "wrs.h"
 #include <stdint.h>
 
 namespace wrs {
 
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+// planes in the ring of per-frame replacement codes (a power of two)
+constexpr int kRingFrames = 16;
+constexpr uint32_t kRingMask = kRingFrames - 1;
 constexpr float kInf = __builtin_huge_valf();
 constexpr float kFltMax = 3.40282346638528859812e+38f;
 
@@ -152,7 +156,28 @@ struct StreamDev {
   int32_t bias;
   int32_t literal;   // 1: the literal n = 1 rule (push_group_literal)
   unsigned long long* replacements;  // running count of slot replacements (stream header)
+  uint8_t* maps;     // ring of replacement-code planes [kRingFrames][plane] (primary buffer)
+  uint32_t* check;   // checked build: bits of the bounds checks that failed (stream header)
 };
+
+// ---------------------------------------------------------------- checked build
+// Compiled with WRS_CHECKED, every group of pixels tests the indices it is
+// about to use (state planes, shared-memory stage, frame, output, flush map,
+// gathered source pixel, bulk-copy ranges) against their buffers first. A
+// failed test sets its bit in the stream's check word (state header + 16) and
+// the access is skipped; nothing traps. wrs_check_status reports the word.
+// Without WRS_CHECKED the tests compile to nothing.
+constexpr uint32_t kChkPlane = 1u, kChkStage = 2u, kChkFrame = 4u, kChkOut = 8u, kChkCopy = 16u,
+                   kChkGather = 32u, kChkStageSize = 64u;
+#ifdef WRS_CHECKED
+__device__ __forceinline__ bool in_bounds(uint32_t* word, bool ok, uint32_t bit) {
+  if (!ok) atomicOr(word, bit);
+  return ok;
+}
+#define WRS_IN(s, cond, bit) ::wrs::in_bounds((s).check, (cond), (bit))
+#else
+#define WRS_IN(s, cond, bit) true
+#endif
 
 struct FrameDev {
   const float* frame;  // [H][pitch]
@@ -161,6 +186,7 @@ struct FrameDev {
   float* out;          // [H][W][3] or null
   float gx, gy;
   uint32_t t;
+  uint32_t map_lo;     // first frame whose codes a folding block still has to apply
 };
 
 // (y, x) of pixel p: y = p / width by a multiply-high with ceil(2^32 / width),
@@ -418,7 +444,156 @@ __device__ __forceinline__ void store_rgb(float* dst, const float (&o)[N][3]) {
   }
 }
 
+// ---------------------------------------------------------------- sample indices
+
+// Replacement codes: the slot that took the frame's sample (0..K-1), that
+// slot plus kCodeFlush when the history was dropped first (every other slot
+// is then empty), or kCodeKeep when the reservoir kept its samples.
+constexpr uint8_t kCodeKeep = 0xFFu, kCodeFlush = 0x80u;
+
+// Sample index of slot j after frame `fr` with code c (v before it).
+__device__ __forceinline__ uint32_t after_code(uint32_t v, int j, uint8_t c, uint32_t fr) {
+  if (c == kCodeKeep) return v;
+  if (c & kCodeFlush) return (c & 0x1Fu) == static_cast<uint32_t>(j) ? fr : kEmpty;
+  return c == static_cast<uint8_t>(j) ? fr : v;
+}
+
+// The band of 256-pixel block b: (b + b/16 + b/256) mod 16. The persistent
+// kernels deal tiles to CTAs in arithmetic progressions whose step (the grid,
+// 152 SMs x CTAs per SM) is a multiple of 8 or 16, so a band of b % 16 would
+// give each CTA all of its folds in one frame out of 16 (the slowest CTA then
+// sets the frame's time). Adding the higher base-16 digits makes each CTA's
+// blocks run through every band: with 152 or 304 CTAs no CTA folds more than
+// 1.05 times its share in any frame.
+__device__ __forceinline__ uint32_t fold_band(int64_t p) {
+  const uint32_t b = static_cast<uint32_t>(p >> 8);
+  return (b + (b >> 4) + (b >> 8)) & kRingMask;
+}
+
+// Whether this frame's push folds pixel p's pending codes into its idx
+// planes: one band of blocks per frame, band(block) == t % ring.
+__device__ __forceinline__ bool folds_now(const FrameDev& f, int64_t p) {
+  return ((fold_band(p) ^ f.t) & kRingMask) == 0u;
+}
+
+// What a fold reads: pixel p's K sample indices (K <= KM) and its ring codes
+// of the frames t-15 .. t-1 (byte k of the 16: frame t-15+k). All loads are
+// issued at once, so a fold costs one memory round trip, and the pipelined
+// kernels issue them before waiting for the tile, hiding even that.
+template <int KM>
+struct FoldIn {
+  uint32_t v[KM];
+  uint32_t code[kRingFrames / 4];
+};
+
+// Capacity of the fold inputs of a kernel instantiated for KT slots (0: any K).
+template <int KT>
+struct FoldCap {
+  static constexpr int value = (KT > 0 && KT <= 8) ? 8 : WRS_MAX_K;
+};
+template <int KT>
+using FoldFor = FoldIn<FoldCap<KT>::value>;
+
+template <int KM>
+__device__ __forceinline__ void fold_load(const StreamDev& s, const uint32_t* idx, int K,
+                                          uint32_t t, int64_t p, FoldIn<KM>& in) {
+  const int64_t pl = s.plane;
+#pragma unroll
+  for (int j = 0; j < KM; ++j) in.v[j] = j < K ? idx[j * pl + p] : kEmpty;
+  uint8_t b[kRingFrames];
+#pragma unroll
+  for (int k = 0; k < kRingFrames - 1; ++k) {
+    const uint32_t fr = t - static_cast<uint32_t>(kRingFrames - 1) + k;
+    b[k] = s.maps[static_cast<int64_t>(fr & kRingMask) * pl + p];
+  }
+  b[kRingFrames - 1] = kCodeKeep;
+#pragma unroll
+  for (int w = 0; w < kRingFrames / 4; ++w)
+    in.code[w] = static_cast<uint32_t>(b[4 * w]) | (static_cast<uint32_t>(b[4 * w + 1]) << 8) |
+                 (static_cast<uint32_t>(b[4 * w + 2]) << 16) |
+                 (static_cast<uint32_t>(b[4 * w + 3]) << 24);
+}
+
+// Applies the loaded codes of frames lo .. t-1 (older ring entries, and
+// entries of frames before lo, are skipped) and then, if c_now is not
+// kCodeKeep, code c_now of frame t; writes pixel p's K indices to `idx`.
+template <int KM>
+__device__ __forceinline__ void fold_store(const StreamDev& s, uint32_t* idx, int K, uint32_t t,
+                                           uint32_t lo, int64_t p, const FoldIn<KM>& in,
+                                           uint8_t c_now) {
+  const int64_t pl = s.plane;
+  uint32_t v[KM];
+#pragma unroll
+  for (int j = 0; j < KM; ++j) v[j] = in.v[j];
+#pragma unroll
+  for (int k = 0; k < kRingFrames - 1; ++k) {
+    const uint32_t fr = t - static_cast<uint32_t>(kRingFrames - 1) + k;
+    const uint8_t c = static_cast<uint8_t>(in.code[k >> 2] >> (8 * (k & 3)));
+    if (fr >= lo && fr < t && c != kCodeKeep) {
+#pragma unroll
+      for (int j = 0; j < KM; ++j) v[j] = after_code(v[j], j, c, fr);
+    }
+  }
+  if (c_now != kCodeKeep) {
+#pragma unroll
+    for (int j = 0; j < KM; ++j) v[j] = after_code(v[j], j, c_now, t);
+  }
+#pragma unroll
+  for (int j = 0; j < KM; ++j)
+    if (j < K) idx[j * pl + p] = v[j];
+}
+
+// This frame's code of pixel p into the ring and, for the band this frame
+// folds, every pending code into the idx planes (from `pre` when the fold's
+// inputs were loaded ahead, else loaded here).
+template <int KT>
+__device__ __forceinline__ void record_code(const StreamDev& s, const FrameDev& f, int64_t p,
+                                            uint8_t c, const FoldFor<KT>* pre) {
+  const int K = KT > 0 ? KT : s.K;
+  s.maps[static_cast<int64_t>(f.t & kRingMask) * s.plane + p] = c;
+  if (!folds_now(f, p)) return;
+  if (pre != nullptr) {
+    fold_store(s, s.idx, K, f.t, f.map_lo, p, *pre, c);
+  } else {
+    FoldFor<KT> in;
+    fold_load(s, s.idx, K, f.t, p, in);
+    fold_store(s, s.idx, K, f.t, f.map_lo, p, in, c);
+  }
+}
+
 // ---------------------------------------------------------------- the pixel group
+
+// Checked build: the indices a group of PX pixels at p0 uses, against their
+// buffers: state-plane entries p0 .. p0+PX-1 (writes, and reads through
+// global planes), source entries at src.at in planes of src.stride entries
+// (the shared-memory stage or the global planes), the pixels' frame rows and
+// columns and the output. True in the default build.
+template <int PX, bool VEC>
+__device__ __forceinline__ bool group_in_bounds(const StreamDev& s, const FrameDev& f, int p0,
+                                                const Src& src, const bool (&valid)[PX],
+                                                const int (&xs)[PX], const int (&ys)[PX]) {
+#ifdef WRS_CHECKED
+  bool ok = WRS_IN(s, p0 >= 0 && static_cast<int64_t>(p0) + PX <= s.plane, kChkPlane);
+  ok = WRS_IN(s, src.at >= 0 && src.at + PX <= src.stride, kChkStage) && ok;
+#pragma unroll
+  for (int i = 0; i < PX; ++i) {
+    if (!valid[i]) continue;
+    ok = WRS_IN(s, ys[i] >= 0 && ys[i] < s.height && xs[i] >= 0 && xs[i] < s.width &&
+                       static_cast<int64_t>(ys[i]) * s.width + xs[i] == static_cast<int64_t>(p0) + i,
+                kChkFrame) && ok;
+    if (f.frame != nullptr && (src.frame == nullptr || src.stride == s.plane))
+      ok = WRS_IN(s, static_cast<int64_t>(ys[i]) * f.pitch + 3 * xs[i] + 3 <=
+                         static_cast<int64_t>(s.height) * f.pitch,
+                  kChkFrame) && ok;
+  }
+  if (VEC && f.out != nullptr)
+    ok = WRS_IN(s, (static_cast<int64_t>(ys[0]) * s.width + xs[0] + PX) * 3 <= 3ll * s.hw, kChkOut) && ok;
+  return ok;
+#else
+  (void)s; (void)f; (void)p0; (void)src; (void)valid; (void)xs; (void)ys;
+  return true;
+#endif
+}
 
 // One thread's group of PX consecutive pixels p0 .. p0+PX-1 (p0 % PX == 0):
 // weight, key, bias, key race over the K slots, fused resolve, stores. Reads
@@ -430,7 +605,8 @@ __device__ __forceinline__ void store_rgb(float* dst, const float (&o)[N][3]) {
 // compiled out.
 template <int KT, bool F16, int PX, bool VEC, bool FOV>
 __device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f, int p0,
-                                          const Src& src, float d_f) {
+                                          const Src& src, float d_f,
+                                          const FoldFor<KT>* pre = nullptr) {
   const int K = KT > 0 ? KT : s.K;
   const int64_t pl = s.plane;
   const int64_t ss = src.stride;
@@ -457,6 +633,8 @@ __device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f,
       if (valid[i]) row_col(s, p, ys[i], xs[i]);
     }
   }
+
+  if (!group_in_bounds<PX, VEC>(s, f, p0, src, valid, xs, ys)) return 0;
 
   // incoming colours
   float rgb[PX][3];
@@ -624,16 +802,18 @@ __device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f,
       for (int j = 0; j < K; ++j) {
         if (j == jm[i]) continue;
         s.key[j * pl + p] = kInf;
-        s.idx[j * pl + p] = kEmpty;
         store_slot<F16>(s.wt, s.col, K, j, pl, p, 0.0f, 0.0f, 0.0f, 0.0f);
       }
     }
     if (repl[i]) {
       const int j = jm[i];
       s.key[j * pl + p] = ks[i];
-      s.idx[j * pl + p] = f.t;
       store_slot<F16>(s.wt, s.col, K, j, pl, p, w[i], rgb[i][0], rgb[i][1], rgb[i][2]);
     }
+    // the sample index goes to the ring as a code
+    const uint8_t code = repl[i] ? static_cast<uint8_t>(jm[i] | (flush[i] ? kCodeFlush : 0u))
+                                 : (flush[i] ? kCodeFlush : kCodeKeep);
+    record_code<KT>(s, f, p, code, PX == 1 ? pre : nullptr);
   }
   int replaced = 0;
 #pragma unroll
@@ -648,7 +828,8 @@ __device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f,
 // resolve and store code as the key race.
 template <bool F16, int PX, bool VEC, bool FOV>
 __device__ __forceinline__ int push_group_literal(const StreamDev& s, const FrameDev& f, int p0,
-                                                  const Src& src, float d_f) {
+                                                  const Src& src, float d_f,
+                                                  const FoldFor<1>* pre = nullptr) {
   const int64_t pl = s.plane;
   const int64_t ss = src.stride;
   const int64_t sa = src.at;
@@ -673,6 +854,7 @@ __device__ __forceinline__ int push_group_literal(const StreamDev& s, const Fram
       if (valid[i]) row_col(s, p, ys[i], xs[i]);
     }
   }
+  if (!group_in_bounds<PX, VEC>(s, f, p0, src, valid, xs, ys)) return 0;
   float rgb[PX][3];
   if constexpr (VEC) {
     load_rgb<PX>(src.frame, rgb);
@@ -775,11 +957,13 @@ __device__ __forceinline__ int push_group_literal(const StreamDev& s, const Fram
   int taken = 0;
 #pragma unroll
   for (int i = 0; i < PX; ++i) {
-    if (!valid[i] || !take[i]) continue;
+    if (!valid[i]) continue;
     const int64_t p = p0 + i;
-    s.idx[p] = f.t;
-    store_slot<F16>(s.wt, s.col, 1, 0, pl, p, w[i], rgb[i][0], rgb[i][1], rgb[i][2]);
-    taken += 1;
+    if (take[i]) {
+      store_slot<F16>(s.wt, s.col, 1, 0, pl, p, w[i], rgb[i][0], rgb[i][1], rgb[i][2]);
+      taken += 1;
+    }
+    record_code<1>(s, f, p, take[i] ? static_cast<uint8_t>(0) : kCodeKeep, PX == 1 ? pre : nullptr);
   }
   return taken;
 }
@@ -789,6 +973,7 @@ template <int KT, bool F16, int PX>
 __device__ __forceinline__ void resolve_group(const StreamDev& s, float* out, int p0) {
   const int K = KT > 0 ? KT : s.K;
   const int64_t pl = s.plane;
+  if (!WRS_IN(s, p0 >= 0 && static_cast<int64_t>(p0) + PX <= pl, kChkPlane)) return;
   float num[PX][3], den[PX];
 #pragma unroll
   for (int i = 0; i < PX; ++i) { num[i][0] = num[i][1] = num[i][2] = 0.0f; den[i] = 0.0f; }

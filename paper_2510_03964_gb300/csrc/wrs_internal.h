@@ -24,6 +24,10 @@ struct wrs_ctx {
   int pipe_ctas;         // pipelined kernel: CTAs per SM (0: as many as fit)
   uint64_t timeout_ns;   // bound on every device-side wait
   uint32_t test_extra_tx;  // > 0 only to exercise the timeout path in tests
+  int failed;             // 1 once wrs_check_status saw a wait give up: the reservoirs are
+                          // undefined until wrs_import_state restores a saved state
+  uint32_t base;          // the idx planes hold every sample index of frames < base; later
+                          // ones are codes in the ring until a push or a fold applies them
 };
 
 constexpr int kDefaultBlock = 256;
@@ -40,6 +44,8 @@ cudaError_t wrs_launch_pipe(const wrs::StreamDev& s, const wrs::FrameDev& f, boo
 void wrs_default_pipe(int K, bool f16, int* px, int* stages);
 
 void wrs_clear_error();
+// WRS_OK, or WRS_ERR_STATE (with the message set) if the context's reservoirs are undefined.
+int wrs_require_usable(const wrs_ctx* x);
 int wrs_fail(int code, const char* fmt, ...);
 int wrs_cuda_fail(cudaError_t e, const char* what);
 int wrs_check_config(const wrs_config* c);
@@ -47,6 +53,11 @@ void wrs_make_layout(const wrs_config* c, wrs_layout* L);
 float wrs_delta(const wrs_config* c);
 wrs::StreamDev wrs_stream_dev(const wrs_ctx* x);
 cudaError_t wrs_init_planes(const wrs_ctx* x, uint8_t* base, cudaStream_t st);
+// First frame whose ring codes the band folded by the next push still applies.
+uint32_t wrs_map_lo(const wrs_ctx* x);
+// Folds every pending ring code into the current idx planes (a kernel on st);
+// afterwards base = t.
+cudaError_t wrs_fold_all(wrs_ctx* x, cudaStream_t st);
 int wrs_effective_px(const wrs_ctx* x, const float* frame, int64_t pitch, const float* out);
 // Validates a foveation source (image, mip buffer, radii, filter) and fills fv.
 int wrs_fov_source(const float* d_img, int64_t pitch, const void* d_mip, size_t mip_bytes,

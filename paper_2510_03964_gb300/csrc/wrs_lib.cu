@@ -39,11 +39,19 @@ int wrs_cuda_fail(cudaError_t e, const char* what) {
   return wrs_fail(WRS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+int wrs_require_usable(const wrs_ctx* x) {
+  if (!x->failed) return WRS_OK;
+  return wrs_fail(WRS_ERR_STATE,
+                  "a device-side wait gave up on this stream, so its reservoirs are undefined: "
+                  "restore a saved state with wrs_import_state first");
+}
+
 // ---------------------------------------------------------------- config, layout
 
 static constexpr int64_t kPlaneAlign = 64;                 // entries; 256 B for 4-byte planes
 static constexpr int64_t kMaxPixels = (1ll << 31) - 64;
 static constexpr int64_t kStatusBytes = 256;                // status header before the planes
+static constexpr int64_t kMapFrames = wrs::kRingFrames;     // ring of replacement-code planes
 
 int wrs_check_config(const wrs_config* c) {
   if (!c) return wrs_fail(WRS_ERR_ARG, "config is NULL");
@@ -85,13 +93,15 @@ void wrs_make_layout(const wrs_config* c, wrs_layout* L) {
     // low halves of the slot weights (uint16), then 8-byte records {r, g, b, w_hi}
     L->wt_off = L->idx_off + c->K * L->plane_bytes4;
     L->col_off = (L->wt_off + c->K * L->plane_bytes_wt + 255) / 256 * 256;
-    L->total_bytes = L->col_off + c->K * L->plane_bytes_col;
   } else {
     // FP32 colour: weight and colour of a slot in one float4 record
     L->wt_off = -1;
     L->col_off = L->idx_off + c->K * L->plane_bytes4;
-    L->total_bytes = L->col_off + c->K * L->plane_bytes_col;
   }
+  // one code byte per pixel and frame for the last kMapFrames frames
+  L->map_off = L->col_off + c->K * L->plane_bytes_col;
+  L->map_frames = kMapFrames;
+  L->total_bytes = L->map_off + kMapFrames * pl;
 }
 
 float wrs_delta(const wrs_config* c) {
@@ -124,7 +134,15 @@ StreamDev wrs_stream_dev(const wrs_ctx* x) {
   s.bias = x->cfg.temporal_bias;
   s.literal = x->cfg.update_rule == WRS_RULE_LITERAL ? 1 : 0;
   s.replacements = reinterpret_cast<unsigned long long*>(x->state + x->lay.status_off + 8);
+  s.maps = x->state + x->lay.map_off;  // the ring stays in the primary buffer
+  s.check = reinterpret_cast<uint32_t*>(x->state + x->lay.status_off + 16);
   return s;
+}
+
+uint32_t wrs_map_lo(const wrs_ctx* x) {
+  const uint32_t back = static_cast<uint32_t>(x->lay.map_frames - 1);
+  const uint32_t oldest = x->t >= back ? x->t - back : 0u;  // oldest frame the ring still holds
+  return x->base > oldest ? x->base : oldest;
 }
 
 uint32_t* wrs_status_word(const wrs_ctx* x) {
@@ -180,6 +198,29 @@ __global__ void init_kernel(StreamDev s) {
       s.key[j * n + i] = wrs::kInf;
       s.idx[j * n + i] = wrs::kEmpty;
       if (s.wt) s.wt[j * n + i] = 0;  // records are zeroed with the colour region
+    }
+  }
+}
+
+// Folds every pending ring code into the idx planes: pixel p's block was
+// last folded by the push of the latest frame below t with that frame % ring
+// == the block's band (if it is not below base); codes of later frames apply.
+__global__ void fold_all_kernel(StreamDev s, uint32_t base, uint32_t t) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < s.hw;
+       p += stride) {
+    uint32_t lo = base;
+    if (t > 0) {
+      const uint32_t d = ((t - 1u) - wrs::fold_band(p)) & wrs::kRingMask;
+      if (t - 1u >= d) {
+        const uint32_t last = (t - 1u) - d;  // the last push that folded this block
+        if (last >= base) lo = last + 1u;
+      }
+    }
+    if (lo < t) {
+      wrs::FoldIn<WRS_MAX_K> in;
+      wrs::fold_load(s, s.idx, s.K, t, p, in);
+      wrs::fold_store(s, s.idx, s.K, t, lo, p, in, wrs::kCodeKeep);
     }
   }
 }
@@ -307,6 +348,15 @@ cudaError_t wrs_launch_push(const StreamDev& s, const FrameDev& f, int block, in
              : launch_push_k<false>(s, f, block, px, st);
 }
 
+cudaError_t wrs_fold_all(wrs_ctx* x, cudaStream_t st) {
+  if (x->base == x->t) return cudaSuccess;
+  const StreamDev s = wrs_stream_dev(x);
+  fold_all_kernel<<<static_cast<unsigned>(x->sms) * 8, 256, 0, st>>>(s, x->base, x->t);
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) x->base = x->t;
+  return e;
+}
+
 // ---------------------------------------------------------------- C-ABI
 
 cudaError_t wrs_init_planes(const wrs_ctx* x, uint8_t* base, cudaStream_t st) {
@@ -352,6 +402,8 @@ extern "C" int wrs_create(const wrs_config* cfg, void* d_state, size_t state_byt
   wrs_default_pipe(cfg->K, cfg->color_fp16 != 0, &x->pipe_px, &x->pipe_stages);
   x->timeout_ns = kDefaultTimeoutNs;
   x->test_extra_tx = 0;
+  x->failed = 0;
+  x->base = 0;
   cudaError_t e = cudaGetDevice(&x->device);
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, x->device);
@@ -385,6 +437,7 @@ extern "C" int wrs_push_frame(wrs_ctx* x, const float* d_frame, int64_t pitch, f
                     static_cast<long long>(pitch));
   if (!std::isfinite(gx) || !std::isfinite(gy))
     return wrs_fail(WRS_ERR_ARG, "gaze must be finite");
+  if (int rc = wrs_require_usable(x)) return rc;
   if (x->t == 0xFFFFFFFFu) return wrs_fail(WRS_ERR_STATE, "frame counter exhausted");
   const StreamDev s = wrs_stream_dev(x);
   FrameDev f;
@@ -395,6 +448,7 @@ extern "C" int wrs_push_frame(wrs_ctx* x, const float* d_frame, int64_t pitch, f
   f.gx = gx;
   f.gy = gy;
   f.t = x->t;
+  f.map_lo = wrs_map_lo(x);
   cudaError_t e;
   if (x->pipe && wrs_pipe_supported(x, d_frame, pitch, d_out)) {
     e = wrs_launch_pipe(s, f, x->cfg.color_fp16 != 0, x->pipe_px, x->pipe_stages, x->sms,
@@ -426,6 +480,7 @@ extern "C" int wrs_push_foveated(wrs_ctx* x, const float* d_img, int64_t img_pit
   if (int rc = wrs_fov_source(d_img, img_pitch, d_mip, mip_bytes, x->cfg.width, x->cfg.height,
                               nradii, radii, filter, &fv))
     return rc;
+  if (int rc = wrs_require_usable(x)) return rc;
   if (x->t == 0xFFFFFFFFu) return wrs_fail(WRS_ERR_STATE, "frame counter exhausted");
   const StreamDev s = wrs_stream_dev(x);
   FrameDev f;
@@ -436,6 +491,7 @@ extern "C" int wrs_push_foveated(wrs_ctx* x, const float* d_img, int64_t img_pit
   f.gx = gx;
   f.gy = gy;
   f.t = x->t;
+  f.map_lo = wrs_map_lo(x);
   int px = x->pipe_px, stages = x->pipe_stages;
   if (px != 1) wrs_default_pipe(x->cfg.K, x->cfg.color_fp16 != 0, &px, &stages);
   cudaError_t e = wrs_launch_pipe_fov(s, f, fv, filter, x->cfg.color_fp16 != 0, stages, x->sms,
@@ -450,6 +506,7 @@ extern "C" int wrs_resolve(wrs_ctx* x, float* d_out, wrs_stream_t stream) {
   wrs_clear_error();
   if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
   if (!d_out || !aligned(d_out, 4)) return wrs_fail(WRS_ERR_ARG, "d_out is NULL or unaligned");
+  if (int rc = wrs_require_usable(x)) return rc;
   const StreamDev s = wrs_stream_dev(x);
   const int px = (x->px == 4) ? 4 : 1;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -497,15 +554,19 @@ extern "C" int wrs_export_state(wrs_ctx* x, void* h_dst, size_t bytes, wrs_strea
     return wrs_fail(WRS_ERR_BUDGET, "destination holds %zu bytes, the state is %lld", bytes,
                     static_cast<long long>(x->lay.total_bytes));
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // the header from the primary buffer, the planes from whichever buffer holds them
+  // complete sample indices first, then the header from the primary buffer and
+  // the planes from whichever buffer holds them
+  cudaError_t e = wrs_fold_all(x, st);
+  if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_export_state: fold");
   const int64_t hdr = x->lay.W_off;
   uint8_t* dst = static_cast<uint8_t*>(h_dst);
-  cudaError_t e = cudaMemcpyAsync(dst, x->state, hdr, cudaMemcpyDeviceToHost, st);
+  e = cudaMemcpyAsync(dst, x->state, hdr, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(dst + hdr, x->planes + hdr, x->lay.total_bytes - hdr,
-                        cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(dst + hdr, x->planes + hdr, x->lay.map_off - hdr, cudaMemcpyDeviceToHost,
+                        st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_export_state");
+  std::memset(dst + x->lay.map_off, 0, static_cast<size_t>(x->lay.total_bytes - x->lay.map_off));
   return WRS_OK;
 }
 
@@ -521,11 +582,13 @@ extern "C" int wrs_import_state(wrs_ctx* x, const void* h_src, size_t bytes,
   const uint8_t* src = static_cast<const uint8_t*>(h_src);
   cudaError_t e = cudaMemcpyAsync(x->state, src, hdr, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(x->planes + hdr, src + hdr, x->lay.total_bytes - hdr,
-                        cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(x->planes + hdr, src + hdr, x->lay.map_off - hdr, cudaMemcpyHostToDevice,
+                        st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_import_state");
   x->t = frame_index;
+  x->base = frame_index;  // imported indices are complete; the ring's codes are stale
+  x->failed = 0;          // the reservoirs are defined again
   return WRS_OK;
 }
 
@@ -599,21 +662,42 @@ extern "C" int wrs_set_wait_limit(wrs_ctx* x, uint64_t timeout_ns, uint32_t test
   return WRS_OK;
 }
 
+extern "C" int wrs_checked_build(void) {
+#ifdef WRS_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
 extern "C" int wrs_check_status(wrs_ctx* x, wrs_stream_t stream) {
   wrs_clear_error();
   if (!x) return wrs_fail(WRS_ERR_ARG, "context is NULL");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  uint32_t word = 0;
-  cudaError_t e = cudaMemcpyAsync(&word, wrs_status_word(x), sizeof word, cudaMemcpyDeviceToHost, st);
+  uint32_t head[5] = {0, 0, 0, 0, 0};  // status word at +0, check word at +16
+  cudaError_t e = cudaMemcpyAsync(head, wrs_status_word(x), sizeof head, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_check_status");
+  const uint32_t word = head[0], bounds = head[4];
+  if (bounds != 0) {
+    e = cudaMemsetAsync(reinterpret_cast<uint8_t*>(wrs_status_word(x)) + 16, 0, sizeof bounds, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_check_status: clear");
+    x->failed = 1;
+    return wrs_fail(WRS_ERR_CHECK,
+                    "checked build: indices outside their buffers were skipped (bits 0x%x: 1 state "
+                    "plane, 2 source/stage entry, 4 frame pixel, 8 output, 16 bulk-copy range, 32 "
+                    "reprojection source, 64 stage size); the reservoirs are undefined",
+                    bounds);
+  }
   if (word == WRS_OK) return WRS_OK;
   e = cudaMemsetAsync(wrs_status_word(x), 0, sizeof word, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_check_status: clear");
+  x->failed = 1;
   return wrs_fail(static_cast<int>(word),
-                  "a device-side wait gave up after %llu ns; frames pushed since the last check "
-                  "may be incomplete",
+                  "a device-side wait gave up after %llu ns: the reservoirs are undefined and "
+                  "further pushes are refused until wrs_import_state restores a saved state",
                   static_cast<unsigned long long>(x->timeout_ns));
 }
 

@@ -18,6 +18,8 @@
 // with wrs_check_status.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "wrs.h"
 #include "wrs_async.cuh"
 #include "wrs_device.cuh"
@@ -61,8 +63,15 @@ __global__ void __launch_bounds__(kPipeThreads, PX == 1 ? 2 : 1)
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
-  if (tid == 0) wrs::init_ring(r, kConsumerWarps);
+  __shared__ uint32_t failed;
+  if (tid == 0) {
+    wrs::init_ring(r, kConsumerWarps);
+    // a wait of an earlier push gave up and the host has not yet seen it: the
+    // reservoirs are undefined, so leave them (and the waits) alone
+    failed = *reinterpret_cast<volatile const uint32_t*>(a.status);
+  }
   __syncthreads();
+  if (failed != 0) return;
 
   const int first = blockIdx.x;
   const int step = gridDim.x;
@@ -76,18 +85,27 @@ __global__ void __launch_bounds__(kPipeThreads, PX == 1 ? 2 : 1)
                             wrs::draw_tile_uniforms_warp<T>(s, f, p0, u, ln);
                             __syncwarp();
                             wrs::issue_tile_copies<T>(s, f, K, cs, resolve, L, st, full, p0,
-                                                      a.extra_tx, ln, FOVF < 0);
+                                                      a.extra_tx, ln, FOVF < 0, r.stage_bytes);
                           });
   } else {
     const float d_f = wrs::fovea_density(s);
-    wrs::consume(r, my_tiles, a.timeout_ns, lane, [&](int it, uint8_t* st, const float* u) {
-      const int64_t p0 = static_cast<int64_t>(first + it * step) * T;
-      if constexpr (FOVF >= 0)
-        replaced +=
-            wrs::compute_tile_fov<KT, F16, PX, T, LIT, FOVF>(s, f, fv, L, st, u, p0, d_f, tid);
-      else
-        replaced += wrs::compute_tile<KT, F16, PX, T, LIT>(s, f, L, st, u, p0, d_f, tid);
-    });
+    wrs::FoldFor<KT> fin;
+    bool folding = false;
+    wrs::consume(
+        r, my_tiles, a.timeout_ns, lane,
+        [&](int it) {
+          const int64_t p0 = static_cast<int64_t>(first + it * step) * T;
+          if constexpr (KT > 0) folding = wrs::prefetch_fold<wrs::FoldCap<KT>::value, PX>(s, f, p0, tid, fin);
+        },
+        [&](int it, uint8_t* st, const float* u) {
+          const int64_t p0 = static_cast<int64_t>(first + it * step) * T;
+          const wrs::FoldFor<KT>* pre = folding ? &fin : nullptr;
+          if constexpr (FOVF >= 0)
+            replaced += wrs::compute_tile_fov<KT, F16, PX, T, LIT, FOVF>(s, f, fv, L, st, u, p0,
+                                                                         d_f, tid, pre);
+          else
+            replaced += wrs::compute_tile<KT, F16, PX, T, LIT>(s, f, L, st, u, p0, d_f, tid, pre);
+        });
   }
   __syncthreads();
   if (warp < kConsumerWarps) wrs::add_warp_count(s.replacements, replaced, lane);
@@ -103,17 +121,22 @@ cudaError_t launch_pipe_t(const StreamDev& s, const FrameDev& f, PipeArgs a, int
   constexpr int T = kConsumerWarps * 32 * PX;
   const StageLayout L = wrs::stage_layout(T, s.K, F16 ? 2 : 4, a.resolve != 0);
   const size_t smem = wrs::ring_bytes(L.bytes, T, a.stages);
-  // per instantiation and device: the largest dynamic shared memory already allowed
+  // per instantiation and device: the largest dynamic shared memory already
+  // allowed; the lock keeps two host threads from lowering each other's limit
   static size_t configured[64] = {};
+  static std::mutex lock;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  if (smem > configured[dev]) {
-    e = cudaFuncSetAttribute(pipe_kernel<KT, F16, PX, LIT, FOVF>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    configured[dev] = smem;
+  {
+    std::lock_guard<std::mutex> hold(lock);
+    if (smem > configured[dev]) {
+      e = cudaFuncSetAttribute(pipe_kernel<KT, F16, PX, LIT, FOVF>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+      if (e != cudaSuccess) return e;
+      configured[dev] = smem;
+    }
   }
   int fit = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, pipe_kernel<KT, F16, PX, LIT, FOVF>,

@@ -118,6 +118,10 @@ __device__ __forceinline__ int reproject_keys(const StreamDev& cur, const Stream
   const float dp = r.depth != nullptr ? r.depth[p] : 0.0f;
   bool ok;
   const int64_t q = source_pixel(cur, r, p, x, y, dp, ok);
+  if (!WRS_IN(cur, q >= 0 && q < cur.hw && p < cur.hw && y < cur.height && x < cur.width &&
+                       static_cast<int64_t>(y) * cur.width + x == p,
+              kChkGather))
+    return 0;
   cp_async4(sW, prev.W + q);
   cp_async4(sP, prev.P + q);
   for (int j = 0; j < K; ++j) {
@@ -259,6 +263,10 @@ __device__ __forceinline__ int reproject_literal(const StreamDev& cur, const Str
 
   bool ok;
   const int64_t q = source_pixel(cur, r, p, x, y, dp, ok);
+  if (!WRS_IN(cur, q >= 0 && q < cur.hw && p < cur.hw && y < cur.height && x < cur.width &&
+                       static_cast<int64_t>(y) * cur.width + x == p,
+              kChkGather))
+    return 0;
   float W = prev.W[q];
   const uint32_t id0 = prev.idx[q];
   float a1[1], r1[1], g1[1], b1[1];
@@ -387,7 +395,7 @@ extern "C" int wrs_set_reprojection_buffer(wrs_ctx* x, void* d_spare, size_t byt
   if (d_spare == nullptr) {
     if (x->planes != x->state) {
       const int64_t hdr = x->lay.W_off;
-      cudaError_t e = cudaMemcpyAsync(x->state + hdr, x->planes + hdr, x->lay.total_bytes - hdr,
+      cudaError_t e = cudaMemcpyAsync(x->state + hdr, x->planes + hdr, x->lay.map_off - hdr,
                                       cudaMemcpyDeviceToDevice, st);
       if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_set_reprojection_buffer: copy back");
       x->planes = x->state;
@@ -405,7 +413,7 @@ extern "C" int wrs_set_reprojection_buffer(wrs_ctx* x, void* d_spare, size_t byt
   if (x->planes != x->state) {
     // the current reservoirs live in the old spare: move them home first
     const int64_t hdr = x->lay.W_off;
-    cudaError_t e = cudaMemcpyAsync(x->state + hdr, x->planes + hdr, x->lay.total_bytes - hdr,
+    cudaError_t e = cudaMemcpyAsync(x->state + hdr, x->planes + hdr, x->lay.map_off - hdr,
                                     cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_set_reprojection_buffer: copy back");
     x->planes = x->state;
@@ -441,8 +449,13 @@ extern "C" int wrs_push_frame_reproject(wrs_ctx* x, const float* d_frame, int64_
     return wrs_fail(WRS_ERR_ARG, "depth buffers must be 4-byte aligned");
   if (d_depth && (!std::isfinite(depth_tol) || depth_tol < 0.0f))
     return wrs_fail(WRS_ERR_ARG, "depth_tol must be finite and >= 0");
+  if (int rc = wrs_require_usable(x)) return rc;
   if (x->t == 0xFFFFFFFFu) return wrs_fail(WRS_ERR_STATE, "frame counter exhausted");
 
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the gather copies whole reservoirs, sample indices included: complete them
+  cudaError_t e = wrs_fold_all(x, st);
+  if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_frame_reproject: fold");
   uint8_t* src_planes = x->planes;
   uint8_t* dst_planes = x->planes == x->state ? x->spare : x->state;
   x->planes = src_planes;
@@ -459,6 +472,7 @@ extern "C" int wrs_push_frame_reproject(wrs_ctx* x, const float* d_frame, int64_
   f.gx = gx;
   f.gy = gy;
   f.t = x->t;
+  f.map_lo = x->t;  // unused: a reprojected push writes every sample index itself
   ReprojDev r;
   r.motion = reinterpret_cast<const float2*>(d_motion);
   r.depth = d_depth;
@@ -469,14 +483,14 @@ extern "C" int wrs_push_frame_reproject(wrs_ctx* x, const float* d_frame, int64_
   const int64_t want = (hw + kThreads - 1) / kThreads;
   const int64_t cap = static_cast<int64_t>(x->sms) * 8 * 16;
   const unsigned grid = static_cast<unsigned>(want < cap ? want : cap);
-  const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool f16 = x->cfg.color_fp16 != 0;
   const bool lit = x->cfg.update_rule == WRS_RULE_LITERAL;
   const bool fov = d_fov != nullptr;
-  cudaError_t e = f16 ? launch_k<true>(x->cfg.K, lit, fov, grid, st, cur, prev, f, r)
-                      : launch_k<false>(x->cfg.K, lit, fov, grid, st, cur, prev, f, r);
+  e = f16 ? launch_k<true>(x->cfg.K, lit, fov, grid, st, cur, prev, f, r)
+          : launch_k<false>(x->cfg.K, lit, fov, grid, st, cur, prev, f, r);
   if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_frame_reproject: launch");
   x->planes = dst_planes;
   x->t += 1;
+  x->base = x->t;  // every index of the new planes is written
   return WRS_OK;
 }

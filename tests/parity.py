@@ -139,6 +139,9 @@ class PairedRun:
         torch.cuda.synchronize()
 
     def compare(self, check_out=True):
+        # WRS_OK: no device-side wait gave up and (in the checked build) no
+        # index or copy range fell outside its buffer
+        assert self.gpu.check_status() == 0, wrs.load().wrs_last_error().decode()
         g = self.gpu.export_state()
         o = self.orc.state()
         compare_states(g, o, self.pixels, self.color_fp16)

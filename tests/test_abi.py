@@ -38,16 +38,18 @@ def test_state_bytes_and_layout(lib):
     hw = 3840 * 2160
     pl = lay.plane_px
     assert pl % 64 == 0 and pl >= hw
-    # FP32 colour: W, P, key[8], idx[8] float planes + 8 float4 {w, r, g, b} record planes
-    assert n == lay.total_bytes == 256 + pl * 4 * (2 + 2 * 8) + pl * 16 * 8
+    # FP32 colour: W, P, key[8], idx[8] float planes + 8 float4 {w, r, g, b} record planes,
+    # then the ring of 16 one-byte replacement-code planes
+    assert lay.map_frames == 16 and lay.map_off == 256 + pl * 4 * (2 + 2 * 8) + pl * 16 * 8
+    assert n == lay.total_bytes == lay.map_off + 16 * pl
     assert lay.status_off == 0 and lay.wt_off == -1 and lay.plane_bytes_col == 16 * pl
-    for off in (lay.W_off, lay.P_off, lay.key_off, lay.idx_off, lay.col_off):
+    for off in (lay.W_off, lay.P_off, lay.key_off, lay.idx_off, lay.col_off, lay.map_off):
         assert off % 256 == 0
     cfg16 = pkg.make_config(3840, 2160, 8, 200.0, color_fp16=True)
     lay16 = pkg.state_layout(cfg16)
     # FP16 colour: W, P, key[8], idx[8] float planes, 8 uint16 planes of the
     # weights' low halves, 8 records {r, g, b, w_hi} of 4 halves
-    assert pkg.state_bytes(cfg16) == 256 + pl * (4 * (2 + 2 * 8) + 2 * 8 + 8 * 8)
+    assert pkg.state_bytes(cfg16) == 256 + pl * (4 * (2 + 2 * 8) + 2 * 8 + 8 * 8) + 16 * pl
     assert lay16.wt_off > 0 and lay16.plane_bytes_col == 8 * pl and lay16.plane_bytes_wt == 2 * pl
     assert lay16.col_off % 256 == 0 and lay.plane_bytes_wt == 0
     # odd K: the weight planes end off a 256-byte boundary and the records start on the next

@@ -37,7 +37,7 @@ def _frames(specs, frames, seed0=1, dev="cuda"):
                                     (4, 1, 0, False), (1, 3, 2, False), (2, 1, 1, True)])
 def test_batch_equals_individual_pushes(launch):
     dev = torch.device("cuda")
-    frames = 7
+    frames = 19  # more frames than the ring of replacement codes holds
     data = _frames(MIX, frames)
     solo = _streams(dev, MIX)
     mixed = _streams(dev, MIX)
@@ -60,6 +60,7 @@ def test_batch_equals_individual_pushes(launch):
             pytest.skip("these stages do not fit in shared memory")
     torch.cuda.synchronize()
     for i in range(len(MIX)):
+        assert mixed[i].check_status() == 0 and solo[i].check_status() == 0
         assert mixed[i].frame_index == solo[i].frame_index == frames
         assert mixed[i].replacements() == solo[i].replacements() > 0
         assert_bits_equal(mixed[i].export_raw(), solo[i].export_raw(), f"stream {i} state")

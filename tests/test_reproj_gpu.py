@@ -58,6 +58,7 @@ class ReprojRun:
         self.prev_depth = depth
 
     def compare(self, check_out=True):
+        assert self.gpu.check_status() == 0, "a wait gave up or the checked build skipped an access"
         torch.cuda.synchronize()
         o = self.orc.state()
         compare_states(self.gpu.export_state(), o, None, self.fp16)

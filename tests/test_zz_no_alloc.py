@@ -39,6 +39,27 @@ def test_noalloc_equals_host_push_on_two_calls(with_fov):
     assert np.array_equal(a.export_raw(), b.export_raw())
 
 
+def test_noalloc_steady_calls_take_no_device_memory():
+    # the first call on the device maps the library's staging array (the
+    # runtime backs it when the module loads); later calls must not change the
+    # device's free memory: any device allocation takes at least a 2 MB page
+    w, h, K = 160, 90, 4
+    fv = Foveator(w, h, (10.0, 25.0), seed=4)
+    gz = gaze_path(w, h, 3, seed=4, model="jitter", jitter_px=8.0)
+    st = wrs.Stream(w, h, K, 10.0, seed=13)
+    frames = [fv.frame(*gz[t])[0].contiguous().pin_memory() for t in range(3)]
+    out = torch.empty((h, w, 3)).pin_memory()
+    st.push_frame_host_noalloc(frames[0], gz[0], out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for t in (1, 2):
+        st.push_frame_host_noalloc(frames[t], gz[t], out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert abs(free0 - free1) < (1 << 20), (free0, free1)
+    assert st.frame_index == 3
+
+
 def test_noalloc_rejects_frames_above_its_staging():
     st = wrs.Stream(8294401, 1, 1, 5.0)
     h_frame = torch.zeros((1, 8294401, 3))
