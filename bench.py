@@ -288,6 +288,10 @@ def run_batched(args, dev):
     from paper_2510_03964_gb300 import autotune
     wl = workload("mix16")
     specs = wl.streams
+    if args.batch_streams < len(specs):
+        # the first stream of each resolution class, then the next ones (profiling cases)
+        order = sorted(range(len(specs)), key=lambda i: (i % 4, i // 4))
+        specs = tuple(specs[i] for i in order[:args.batch_streams])
     nfr = 4
     frames, gazes = [], []
     for s in specs:
@@ -309,18 +313,22 @@ def run_batched(args, dev):
     warm = max(3, args.batch_warmup)
     counts = {}
 
-    def timed(fn, rounds, streams):
+    pixels = sum(s.pixels for s in specs)
+
+    def timed(fn, rounds, streams, label):
         for r in range(warm):
             fn(r)
         torch.cuda.synchronize()
         r0 = sum(x.replacements(stream=stream) for x in streams)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(label)  # lets a profiler select the timed rounds
         a.record(stream)
         for r in range(rounds):
             fn(warm + r)
         b.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
-        counts["rho"] = (sum(x.replacements(stream=stream) for x in streams) - r0) / float(wl.pixels * rounds)
+        counts["rho"] = (sum(x.replacements(stream=stream) for x in streams) - r0) / float(pixels * rounds)
         return a.elapsed_time(b) / rounds
 
     sts = make()
@@ -330,7 +338,7 @@ def run_batched(args, dev):
     def batched_round(t):
         batch.push(sts, [f[t % nfr] for f in frames], [g[t % nfr] for g in gazes], outs=outs, stream=stream)
 
-    ms_batch = timed(batched_round, args.batch_rounds, sts)
+    ms_batch = timed(batched_round, args.batch_rounds, sts, "batched_timed")
     rho = counts["rho"]
     for x in sts:
         x.close()
@@ -340,7 +348,7 @@ def run_batched(args, dev):
         for i, x in enumerate(sts2):
             x.push_frame(frames[i][t % nfr], gazes[i][t % nfr], None, outs[i], stream=stream)
 
-    ms_solo = timed(solo_round, args.batch_rounds, sts2)
+    ms_solo = timed(solo_round, args.batch_rounds, sts2, "launches_timed")
     for x in sts2:
         x.close()
     batch.close()
@@ -349,10 +357,12 @@ def run_batched(args, dev):
                       for s in specs)
     achieved = bytes_round / (ms_batch * 1e-3) / 1e9
     del frames, outs
-    return {"workload": wl.description, "pixels_per_round": wl.pixels, "rounds": args.batch_rounds,
+    desc = wl.description if len(specs) == len(wl.streams) else (
+        f"{len(specs)} streams of the mix: " + ", ".join(f"{s.width}x{s.height} K={s.K}" for s in specs))
+    return {"workload": desc, "pixels_per_round": pixels, "rounds": args.batch_rounds,
             "warmup_rounds": warm,
             "ms_per_round_batched": round(ms_batch, 4), "ms_per_round_16_launches": round(ms_solo, 4),
-            "mpx_updates_per_s": round(wl.pixels / (ms_batch * 1e-3) / 1e6, 1),
+            "mpx_updates_per_s": round(pixels / (ms_batch * 1e-3) / 1e6, 1),
             "replacement_rate": round(rho, 4),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4)},
@@ -588,18 +598,28 @@ def run_reprojection(args, dev):
 
 
 def run_serving(args, dev):
-    """The 64-viewer serving trace at the workload's frame rates (72-120 Hz per
-    viewer) and at an overload (200-300 Hz), batched vs one launch per frame;
-    then the workload's rates with every frame foveated on the device from the
-    viewer's rendered image (requests carry only a gaze)."""
+    """The 64-viewer serving workload as configured: viewers of the four
+    resolution classes (K = 8 / 4, FP16 colour) join and leave over
+    args.serve seconds, each sending frames as a Poisson process at its rate
+    in U[72, 120] Hz, admitted under a 60 GB budget, every frame resolved into
+    the viewer's output; batched (continuous batching) vs one launch per
+    frame, for frames made beforehand and for frames foveated on the device
+    per request. Then an overload (200-300 Hz per viewer) for a shorter
+    args.serve_overload seconds; frames waiting past the 20 ms deadline are
+    shed."""
     from paper_2510_03964_gb300 import serve
     out = {}
-    for name, rate, source in (("rates_72_120hz", (72.0, 120.0), "frames"),
-                               ("overload_200_300hz", (200.0, 300.0), "frames"),
-                               ("rates_72_120hz_foveated_on_device", (72.0, 120.0), "render")):
-        out[name] = serve.serve_compare(n_viewers=64, duration_s=args.serve, budget_gb=60.0, seed=0,
-                                        device=dev, rate_hz=rate, source=source)
+    runs = [("rates_72_120hz", (72.0, 120.0), "frames", args.serve),
+            ("rates_72_120hz_foveated_on_device", (72.0, 120.0), "render", args.serve)]
+    if args.serve_overload > 0:
+        runs.append(("overload_200_300hz", (200.0, 300.0), "frames", args.serve_overload))
+    for name, rate, source, secs in runs:
+        out[name] = serve.serve_compare(n_viewers=64, duration_s=secs, budget_gb=60.0, seed=0,
+                                        device=dev, rate_hz=rate, source=source, deadline_ms=20.0)
         torch.cuda.empty_cache()
+    out["note"] = ("peak_device_gb counts each admitted viewer's reservoir state and output buffer "
+                   "against the 60 GB budget; viewers_queued_max = 0 means the configured mix never "
+                   "filled it")
     return out
 
 
@@ -973,6 +993,8 @@ def main():
     ap.add_argument("--batch-warmup", type=int, default=240,
                     help="untimed rounds before the timed ones: one pass of the workload's 240 "
                          "frames, the stream age of the single-stream line's timed frames")
+    ap.add_argument("--batch-streams", type=int, default=16,
+                    help="streams of the mix in the batched section (fewer: profiling cases)")
     ap.add_argument("--batch-rounds", type=int, default=200,
                     help="rounds of the 16-stream batched workload (0 skips it)")
     ap.add_argument("--fov-reps", type=int, default=50,
@@ -983,8 +1005,11 @@ def main():
     ap.add_argument("--reproj-workload", default="4k_pan", choices=["4k_pan", "hd_pan"])
     ap.add_argument("--reproj-frames", type=int, default=32,
                     help="distinct rendered frames of the pan, cycled")
-    ap.add_argument("--serve", type=float, default=8.0,
-                    help="seconds of the 64-viewer serving trace per mode and load (0 skips it)")
+    ap.add_argument("--serve", type=float, default=60.0,
+                    help="seconds of the 64-viewer serving trace at the configured rates, per mode "
+                         "and frame source (0 skips the serving section)")
+    ap.add_argument("--serve-overload", type=float, default=10.0,
+                    help="seconds of the overload trace (200-300 Hz per viewer) per mode")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

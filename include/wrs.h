@@ -55,6 +55,10 @@ extern "C" {
 #define WRS_RULE_KEYS 0
 #define WRS_RULE_LITERAL 1
 #define WRS_EMPTY_SLOT 0xFFFFFFFFu /* sample index of an unoccupied slot */
+/* foveation post-process (Sec. 4.3): mip levels and reconstruction filters */
+#define WRS_MAX_MIP_LEVELS 6   /* level 0 (the image) .. level 5 (32 x 32 blocks) */
+#define WRS_FILTER_BOX 0       /* nearest lookup of the level's block mean */
+#define WRS_FILTER_BILINEAR 1  /* bilinear filtering of the level's block means */
 
 typedef struct wrs_ctx wrs_ctx;
 typedef void* wrs_stream_t; /* cudaStream_t */
@@ -342,6 +346,30 @@ int wrs_push_batch(wrs_batch* batch, int n, wrs_ctx* const* ctxs, const float* c
                    const float* gaze_xy, const uint8_t* const* d_fov_maps, float* const* d_outs,
                    wrs_stream_t stream);
 
+/* A rendered image and its mip levels: the source a stream's frame is
+ * foveated from (Sec. 4.3), as wrs_foveate / wrs_push_foveated take it. */
+typedef struct {
+  const float* d_img;          /* device [height][img_pitch_elems] RGB floats, 4-byte aligned */
+  int64_t img_pitch_elems;     /* >= 3 * width */
+  const void* d_mip;           /* device mip buffer (wrs_mip_build) with >= nradii + 1 levels */
+  size_t mip_bytes;
+  int32_t nradii;              /* 1 .. WRS_MAX_MIP_LEVELS - 1 */
+  float radii[WRS_MAX_MIP_LEVELS - 1]; /* ring radii in pixels, ascending; [0] the fovea */
+} wrs_fov_source;
+
+/* wrs_push_batch with every frame foveated on read (wrs_push_foveated's
+ * update, batched): stream i's frame is foveated from sources[i] for its
+ * gaze with `filter` (WRS_FILTER_*) by the update kernel itself, so no frame
+ * is written to memory and no foveation launch precedes the batch. Results
+ * are bit-identical to wrs_push_foveated of each stream alone (and so to
+ * wrs_foveate + wrs_push_frame). Needs width % 4 == 0 and 16-byte aligned
+ * outputs; always one pixel per thread (256-pixel tiles). Errors: as
+ * wrs_push_batch and wrs_foveate (nothing is launched on error). */
+int wrs_push_batch_foveated(wrs_batch* batch, int n, wrs_ctx* const* ctxs,
+                            const wrs_fov_source* sources, int32_t filter, const float* gaze_xy,
+                            const uint8_t* const* d_fov_maps, float* const* d_outs,
+                            wrs_stream_t stream);
+
 /* Slot replacements since create (over all pixels and frames; the stream's
  * reservoir churn: a pixel whose candidate entered a slot counts once per
  * frame). Waits for `stream`. */
@@ -394,9 +422,6 @@ int wrs_push_frame_reproject(wrs_ctx* ctx, const float* d_frame, int64_t frame_p
  * filtering. These calls produce, on the device, the foveated frames and
  * ring maps that wrs_push_frame consumes, from a full-resolution image.
  * ------------------------------------------------------------------------ */
-#define WRS_MAX_MIP_LEVELS 6   /* level 0 (the image) .. level 5 (32 x 32 blocks) */
-#define WRS_FILTER_BOX 0       /* nearest lookup of the level's block mean */
-#define WRS_FILTER_BILINEAR 1  /* bilinear filtering of the level's block means */
 
 /* Where each level of a mip buffer lives. Level L >= 1 holds one texel per
  * aligned 2^L x 2^L block of the image, [height[L]][width[L]] texels of

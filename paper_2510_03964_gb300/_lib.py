@@ -35,6 +35,12 @@ WRS_MAX_MIP_LEVELS = 6
 WRS_FILTER_BOX, WRS_FILTER_BILINEAR = 0, 1
 
 
+class WrsFovSource(C.Structure):
+    _fields_ = [("d_img", C.c_void_p), ("img_pitch_elems", C.c_int64), ("d_mip", C.c_void_p),
+                ("mip_bytes", C.c_size_t), ("nradii", C.c_int32),
+                ("radii", C.c_float * (WRS_MAX_MIP_LEVELS - 1))]
+
+
 class WrsMipLayout(C.Structure):
     _fields_ = [("levels", C.c_int32), ("width", C.c_int32 * WRS_MAX_MIP_LEVELS),
                 ("height", C.c_int32 * WRS_MAX_MIP_LEVELS), ("offset", C.c_int64 * WRS_MAX_MIP_LEVELS),
@@ -65,6 +71,7 @@ SIGNATURES = {
     "wrs_batch_set_launch": (_I, [_V, _I, _I, _I, _I]),
     "wrs_batch_get_launch": (_I, [_V, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "wrs_push_batch": (_I, [_V, _I, _V, _V, _V, _V, _V, _V]),
+    "wrs_push_batch_foveated": (_I, [_V, _I, _V, _V, C.c_int32, _V, _V, _V, _V]),
     "wrs_get_stats": (_I, [_V, C.POINTER(C.c_uint64), _V]),
     "wrs_set_reprojection_buffer": (_I, [_V, _V, C.c_size_t, _V]),
     "wrs_push_frame_reproject": (_I, [_V, _V, C.c_int64, C.c_float, C.c_float, _V, _V, _V, C.c_float,

@@ -17,159 +17,10 @@
 #include <new>
 
 #include "wrs.h"
-#include "wrs_async.cuh"
-#include "wrs_device.cuh"
+#include "wrs_batch_kernel.cuh"
 #include "wrs_internal.h"
 
-using wrs::FrameDev;
-using wrs::StageLayout;
-using wrs::StreamDev;
-
 namespace {
-
-constexpr int kMaxBatch = WRS_MAX_BATCH;
-
-struct BatchEntry {
-  StreamDev s;
-  FrameDev f;
-  uint32_t* status;
-  int tile0;   // first global tile of this stream
-  int code;    // arithmetic variant: 0 K=4 f16, 1 K=8 f16, 2 K=4 f32, 3 K=8 f32, 4 any K f16,
-               // 5 any K f32, 6 literal f16, 7 literal f32
-};
-
-// The slot records are staged when the fused resolve needs them or the full
-// temporal bias forms the history's resolved colour from them.
-__device__ __forceinline__ bool stage_records(const BatchEntry& e) {
-  return e.f.out != nullptr || e.s.bias == 2;
-}
-
-struct BatchArgs {
-  int n;
-  int ntiles;
-  int stages;
-  uint32_t stage_bytes;  // largest stage of any stream in the batch
-  uint64_t timeout_ns;
-  BatchEntry e[kMaxBatch];
-};
-// kernel parameters may take up to 32764 bytes on sm_70 and later (CUDA 12.1+)
-static_assert(sizeof(BatchArgs) <= 32000, "batch descriptor too large for a kernel parameter");
-
-__device__ __forceinline__ int entry_of(const BatchArgs& a, int g) {
-  int lo = 0, hi = a.n - 1;  // last entry with tile0 <= g
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (a.e[mid].tile0 <= g) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ bool entry_f16(const BatchEntry& e) {
-  return e.code == 0 || e.code == 1 || e.code == 4 || e.code == 6;
-}
-
-constexpr int kConsumerWarps = 8;
-constexpr int kBatchThreads = (kConsumerWarps + 1) * 32;
-
-// Arithmetic families: a batch whose streams all use FP16 colour with K = 4
-// or 8 (the serving mix) or all FP32 colour with K = 4 or 8 gets a kernel
-// holding only those two variants; any other mix gets the kernel with all.
-constexpr int kFamF16K48 = 0, kFamF32K48 = 1, kFamAll = 2;
-
-// Warp-specialised like the single-stream pipelined kernel: warp 8 draws each
-// tile's uniforms and issues its copies, warps 0..7 compute it.
-template <int PX, int FAM>
-__global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
-    batch_kernel(const __grid_constant__ BatchArgs a) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ unsigned long long replaced_s[kMaxBatch];  // per stream, this CTA
-  __shared__ float d_f_s[kMaxBatch];                    // per stream: density at the fovea edge
-  __shared__ uint32_t failed_s[kMaxBatch];              // per stream: an earlier wait gave up
-  constexpr int T = kConsumerWarps * 32 * PX;
-  const wrs::Ring r = wrs::make_ring(smem, a.stage_bytes, T, a.stages);
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5;
-  const int lane = tid & 31;
-  if (tid == 0) wrs::init_ring(r, kConsumerWarps);
-  if (tid < kMaxBatch) replaced_s[tid] = 0;
-  // each stream's Eq. (phat) normaliser, once per CTA instead of once per tile
-  if (tid < a.n) {
-    d_f_s[tid] = wrs::fovea_density(a.e[tid].s);
-    // a stream whose earlier push timed out (not yet seen by the host) has
-    // undefined reservoirs: its tiles are copied but not computed or written
-    failed_s[tid] = *reinterpret_cast<volatile const uint32_t*>(a.e[tid].status);
-  }
-  __syncthreads();
-
-  const int first = blockIdx.x, step = gridDim.x;
-  const int my_tiles = first < a.ntiles ? (a.ntiles - 1 - first) / step + 1 : 0;
-  int issued = 0;
-  if (warp == kConsumerWarps) {
-    issued = wrs::produce(r, my_tiles, a.timeout_ns, lane,
-                          [&](int it, uint8_t* st, float* u, uint64_t* full, int ln) {
-                            const int g = first + it * step;
-                            const BatchEntry& e = a.e[entry_of(a, g)];
-                            const int64_t p0 = static_cast<int64_t>(g - e.tile0) * T;
-                            const int cs = entry_f16(e) ? 2 : 4;
-                            const bool resolve = stage_records(e);
-                            const StageLayout L = wrs::stage_layout(T, e.s.K, cs, resolve);
-                            wrs::draw_tile_uniforms_warp<T>(e.s, e.f, p0, u, ln);
-                            __syncwarp();
-                            wrs::issue_tile_copies<T>(e.s, e.f, e.s.K, cs, resolve, L, st, full,
-                                                      p0, 0u, ln, true, r.stage_bytes);
-                          });
-  } else {
-    // fold inputs of entries that compute with K = 4 or 8 (or the literal
-    // rule), loaded before the wait; the generic-K arithmetic loads its own
-    wrs::FoldIn<8> fin;
-    bool folding = false;
-    wrs::consume(r, my_tiles, a.timeout_ns, lane, [&](int it) {
-      const int g = first + it * step;
-      const BatchEntry& e = a.e[entry_of(a, g)];
-      const int64_t p0 = static_cast<int64_t>(g - e.tile0) * T;
-      folding = (e.code < 4 || e.code > 5) && wrs::prefetch_fold<8, PX>(e.s, e.f, p0, tid, fin);
-    }, [&](int it, const uint8_t* st, const float* u) {
-      const int g = first + it * step;
-      const int ei = entry_of(a, g);
-      const BatchEntry& e = a.e[ei];
-      const int64_t p0 = static_cast<int64_t>(g - e.tile0) * T;
-      const bool resolve = stage_records(e);
-      const float d_f = d_f_s[ei];
-      if (failed_s[ei] != 0) return;
-      const wrs::FoldIn<8>* pre = folding ? &fin : nullptr;
-      int rc;
-      if constexpr (FAM == kFamF16K48) {
-        rc = e.code == 0
-                 ? wrs::compute_tile<4, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 2, resolve), st, u, p0, d_f, tid, pre)
-                 : wrs::compute_tile<8, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 2, resolve), st, u, p0, d_f, tid, pre);
-      } else if constexpr (FAM == kFamF32K48) {
-        rc = e.code == 2
-                 ? wrs::compute_tile<4, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 4, resolve), st, u, p0, d_f, tid, pre)
-                 : wrs::compute_tile<8, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 4, resolve), st, u, p0, d_f, tid, pre);
-      } else {
-        switch (e.code) {
-        case 0: rc = wrs::compute_tile<4, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 2, resolve), st, u, p0, d_f, tid, pre); break;
-        case 1: rc = wrs::compute_tile<8, true, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 2, resolve), st, u, p0, d_f, tid, pre); break;
-        case 2: rc = wrs::compute_tile<4, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 4, 4, resolve), st, u, p0, d_f, tid, pre); break;
-        case 3: rc = wrs::compute_tile<8, false, PX, T>(e.s, e.f, wrs::stage_layout(T, 8, 4, resolve), st, u, p0, d_f, tid, pre); break;
-        case 4: rc = wrs::compute_tile<0, true, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 2, resolve), st, u, p0, d_f, tid); break;
-        case 6: rc = wrs::compute_tile<1, true, PX, T, true>(e.s, e.f, wrs::stage_layout(T, 1, 2, resolve), st, u, p0, d_f, tid, pre); break;
-        case 7: rc = wrs::compute_tile<1, false, PX, T, true>(e.s, e.f, wrs::stage_layout(T, 1, 4, resolve), st, u, p0, d_f, tid, pre); break;
-        default: rc = wrs::compute_tile<0, false, PX, T>(e.s, e.f, wrs::stage_layout(T, e.s.K, 4, resolve), st, u, p0, d_f, tid); break;
-        }
-      }
-      const unsigned c = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(rc));
-      if (lane == 0 && c != 0) atomicAdd(&replaced_s[ei], static_cast<unsigned long long>(c));
-    });
-  }
-  __syncthreads();
-  if (tid < a.n && replaced_s[tid] != 0) atomicAdd(a.e[tid].s.replacements, replaced_s[tid]);
-  if (wrs::flag_raised(r)) {
-    if (warp == kConsumerWarps) wrs::drain(r, issued, a.timeout_ns);
-    // the batch ran out of time as a whole: report it on every stream
-    if (tid < a.n) atomicExch(a.e[tid].status, static_cast<uint32_t>(WRS_ERR_TIMEOUT));
-  }
-}
 
 template <int PX>
 const void* batch_fn(int fam) {
@@ -188,9 +39,14 @@ const void* batch_kernel_for(int px, int fam) {
   }
 }
 
-constexpr int kSlots = 9;  // 3 pixels-per-thread choices x 3 families
+// 3 pixels-per-thread choices x 3 families, then 3 families x 2 filters of
+// the foveating form (one pixel per thread)
+constexpr int kSlots = 15;
 
 }  // namespace
+
+// The foveating variants (wrs_batch_fov.cu): family x filter.
+const void* wrs_batch_fov_kernel(int fam, int filter);
 
 struct wrs_batch {
   int max_streams;
@@ -285,15 +141,22 @@ static int code_of(const wrs_config& c) {
   return f16 ? 4 : 5;
 }
 
-extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
-                              const float* const* d_frames, const float* gaze_xy,
-                              const uint8_t* const* d_fov_maps, float* const* d_outs,
-                              wrs_stream_t stream) {
-  if (!b || !ctxs || !d_frames || !gaze_xy) return wrs_fail(WRS_ERR_ARG, "NULL argument");
+// Validates and launches one batch; sources == NULL: the frames are in
+// d_frames; else stream i's frame is foveated on read from sources[i] with
+// `filter` (d_frames unused).
+static int push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs, const float* const* d_frames,
+                      const wrs_fov_source* sources, int32_t filter, const float* gaze_xy,
+                      const uint8_t* const* d_fov_maps, float* const* d_outs, wrs_stream_t stream) {
+  const bool fov = sources != nullptr;
+  if (!b || !ctxs || (!d_frames && !fov) || !gaze_xy) return wrs_fail(WRS_ERR_ARG, "NULL argument");
   if (n < 1 || n > b->max_streams)
     return wrs_fail(WRS_ERR_ARG, "n must be in 1..%d (got %d)", b->max_streams, n);
+  if (fov && filter != WRS_FILTER_BOX && filter != WRS_FILTER_BILINEAR)
+    return wrs_fail(WRS_ERR_ARG, "filter must be WRS_FILTER_BOX or WRS_FILTER_BILINEAR");
   BatchArgs& a = *b->args;
-  const int T = 256 * b->px;
+  // the foveating form takes one pixel per thread (256-pixel tiles)
+  const int px = fov ? 1 : b->px;
+  const int T = 256 * px;
   int64_t tiles = 0;
   uint32_t stage_bytes = 0;
   int device = -1;
@@ -304,13 +167,27 @@ extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
       if (ctxs[j] == x) return wrs_fail(WRS_ERR_ARG, "stream %d appears twice in the batch", i);
     if (device < 0) device = x->device;
     if (x->device != device) return wrs_fail(WRS_ERR_ARG, "all streams of a batch must share a device");
-    const float* fr = d_frames[i];
     float* out = d_outs ? d_outs[i] : nullptr;
-    if (!fr || !wrs_pipe_supported(x, fr, 3 * static_cast<int64_t>(x->cfg.width), out))
-      return wrs_fail(WRS_ERR_ARG,
-                      "stream %d: batched frames need width %% 4 == 0 and 16-byte aligned, "
-                      "unpadded frame and out",
-                      i);
+    const float* fr = nullptr;
+    BatchEntry& e = a.e[i];
+    if (fov) {
+      // foveated on read: the stream's own source, checked as wrs_foveate checks it
+      if (x->cfg.width % 4 != 0 || (out && (reinterpret_cast<uintptr_t>(out) & 15u)))
+        return wrs_fail(WRS_ERR_ARG, "stream %d: foveating batches need width %% 4 == 0 and a "
+                        "16-byte aligned out", i);
+      const wrs_fov_source& src = sources[i];
+      if (int rc = wrs_fov_check_source(src.d_img, src.img_pitch_elems, src.d_mip, src.mip_bytes,
+                                  x->cfg.width, x->cfg.height, src.nradii, src.radii, filter, &e.fv))
+        return rc;
+    } else {
+      fr = d_frames[i];
+      if (!fr || !wrs_pipe_supported(x, fr, 3 * static_cast<int64_t>(x->cfg.width), out))
+        return wrs_fail(WRS_ERR_ARG,
+                        "stream %d: batched frames need width %% 4 == 0 and 16-byte aligned, "
+                        "unpadded frame and out",
+                        i);
+      e.fv = wrs::FovDev{};
+    }
     const float gx = gaze_xy[2 * i], gy = gaze_xy[2 * i + 1];
     if (!std::isfinite(gx) || !std::isfinite(gy))
       return wrs_fail(WRS_ERR_ARG, "stream %d: gaze must be finite", i);
@@ -318,7 +195,6 @@ extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
     if (wrs_require_usable(x) != WRS_OK)
       return wrs_fail(WRS_ERR_STATE, "stream %d: a device-side wait gave up on it; restore a saved "
                       "state with wrs_import_state first", i);
-    BatchEntry& e = a.e[i];
     e.s = wrs_stream_dev(x);
     e.f.frame = fr;
     e.f.pitch = 3 * static_cast<int64_t>(x->cfg.width);
@@ -356,8 +232,8 @@ extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
   a.timeout_ns = ctxs[0]->timeout_ns;
 
   const int fam = family_of(a);
-  const int slot = px_slot(b->px) * 3 + fam;
-  const void* fn = batch_kernel_for(b->px, fam);
+  const int slot = fov ? 9 + fam * 2 + filter : px_slot(px) * 3 + fam;
+  const void* fn = fov ? wrs_batch_fov_kernel(fam, filter) : batch_kernel_for(px, fam);
   cudaError_t e = cudaSuccess;
   if (b->device != device) {
     // a new device: drop graphs and attribute settings made for another one
@@ -375,12 +251,12 @@ extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
     // limit it was instantiated under, and later batches may need larger stages
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kSmemBudget));
-    if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_batch: shared memory attribute");
+    if (e != cudaSuccess) return wrs_cuda_fail(e, "push_batch: shared memory attribute");
     b->configured_smem[slot] = kSmemBudget;
   }
   int fit = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, kBatchThreads, smem);
-  if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_batch: occupancy");
+  if (e != cudaSuccess) return wrs_cuda_fail(e, "push_batch: occupancy");
   if (fit < 1) return wrs_fail(WRS_ERR_ARG, "batch kernel does not fit on an SM");
   const int per_sm = b->ctas_per_sm > 0 && b->ctas_per_sm < fit ? b->ctas_per_sm : fit;
   const int64_t want = static_cast<int64_t>(ctxs[0]->sms) * per_sm;
@@ -412,14 +288,32 @@ extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
       e = cudaGraphCreate(&b->graph[slot], 0);
       if (e == cudaSuccess) e = cudaGraphAddKernelNode(&b->node[slot], b->graph[slot], nullptr, 0, &kp);
       if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[slot], b->graph[slot], 0);
-      if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_batch: graph build");
+      if (e != cudaSuccess) return wrs_cuda_fail(e, "push_batch: graph build");
     }
     e = cudaGraphLaunch(b->exec[slot], st);
-    if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_batch: graph launch");
+    if (e != cudaSuccess) return wrs_cuda_fail(e, "push_batch: graph launch");
   } else {
     e = cudaLaunchKernel(fn, kp.gridDim, kp.blockDim, params, smem, st);
-    if (e != cudaSuccess) return wrs_cuda_fail(e, "wrs_push_batch: launch");
+    if (e != cudaSuccess) return wrs_cuda_fail(e, "push_batch: launch");
   }
   for (int i = 0; i < n; ++i) ctxs[i]->t += 1;
   return WRS_OK;
+}
+
+extern "C" int wrs_push_batch(wrs_batch* b, int n, wrs_ctx* const* ctxs,
+                              const float* const* d_frames, const float* gaze_xy,
+                              const uint8_t* const* d_fov_maps, float* const* d_outs,
+                              wrs_stream_t stream) {
+  wrs_clear_error();
+  return push_batch(b, n, ctxs, d_frames, nullptr, WRS_FILTER_BOX, gaze_xy, d_fov_maps, d_outs,
+                    stream);
+}
+
+extern "C" int wrs_push_batch_foveated(wrs_batch* b, int n, wrs_ctx* const* ctxs,
+                                       const wrs_fov_source* sources, int32_t filter,
+                                       const float* gaze_xy, const uint8_t* const* d_fov_maps,
+                                       float* const* d_outs, wrs_stream_t stream) {
+  wrs_clear_error();
+  if (!sources) return wrs_fail(WRS_ERR_ARG, "sources is NULL");
+  return push_batch(b, n, ctxs, nullptr, sources, filter, gaze_xy, d_fov_maps, d_outs, stream);
 }

@@ -291,7 +291,7 @@ extern "C" int wrs_mip_build(const float* d_img, int64_t pitch, int32_t width, i
   return e == cudaSuccess ? WRS_OK : wrs_cuda_fail(e, "wrs_mip_build: launch");
 }
 
-int wrs_fov_source(const float* d_img, int64_t pitch, const void* d_mip, size_t mip_bytes,
+int wrs_fov_check_source(const float* d_img, int64_t pitch, const void* d_mip, size_t mip_bytes,
                    int32_t width, int32_t height, int32_t nradii, const float* radii,
                    int32_t filter, FovDev* out) {
   if (int rc = check_image(width, height)) return rc;
@@ -335,7 +335,7 @@ extern "C" int wrs_foveate(const float* d_img, int64_t pitch, const void* d_mip,
   if (frame_pitch < 3 * (int64_t)width)
     return wrs_fail(WRS_ERR_ARG, "pitches must be >= 3 * width");
   FovArgs a{};
-  if (int rc = wrs_fov_source(d_img, pitch, d_mip, mip_bytes, width, height, nradii, radii, filter,
+  if (int rc = wrs_fov_check_source(d_img, pitch, d_mip, mip_bytes, width, height, nradii, radii, filter,
                               &a.fv))
     return rc;
   a.frame = d_frame;

@@ -60,7 +60,7 @@ uint32_t wrs_map_lo(const wrs_ctx* x);
 cudaError_t wrs_fold_all(wrs_ctx* x, cudaStream_t st);
 int wrs_effective_px(const wrs_ctx* x, const float* frame, int64_t pitch, const float* out);
 // Validates a foveation source (image, mip buffer, radii, filter) and fills fv.
-int wrs_fov_source(const float* d_img, int64_t pitch, const void* d_mip, size_t mip_bytes,
+int wrs_fov_check_source(const float* d_img, int64_t pitch, const void* d_mip, size_t mip_bytes,
                    int32_t width, int32_t height, int32_t nradii, const float* radii,
                    int32_t filter, wrs::FovDev* fv);
 // The pipelined kernel foveating the frame as it reads it (filter: WRS_FILTER_*).

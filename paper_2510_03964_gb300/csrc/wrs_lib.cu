@@ -477,7 +477,7 @@ extern "C" int wrs_push_foveated(wrs_ctx* x, const float* d_img, int64_t img_pit
   if (!std::isfinite(gx) || !std::isfinite(gy))
     return wrs_fail(WRS_ERR_ARG, "gaze must be finite");
   wrs::FovDev fv;
-  if (int rc = wrs_fov_source(d_img, img_pitch, d_mip, mip_bytes, x->cfg.width, x->cfg.height,
+  if (int rc = wrs_fov_check_source(d_img, img_pitch, d_mip, mip_bytes, x->cfg.width, x->cfg.height,
                               nradii, radii, filter, &fv))
     return rc;
   if (int rc = wrs_require_usable(x)) return rc;

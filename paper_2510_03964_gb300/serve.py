@@ -1,24 +1,36 @@
 """Serving many viewers' foveated frame streams on one GPU.
 
-Viewers join and leave over time; each sends frames as a Poisson process.
-Every admitted viewer's reservoirs stay resident in HBM, and viewers are
-admitted while their reservoir bytes fit under an HBM budget (the rest wait
-in a FIFO queue and are admitted as others leave; frames a viewer sends before
+Viewers join and leave over time; each sends frames as a Poisson process,
+and every frame returns the viewer's resolved frame (the update and the
+resolve in one pass, into the viewer's output buffer). Every admitted
+viewer's reservoirs and output stay resident in HBM, and viewers are admitted
+while their device bytes (reservoir state and output) fit under an HBM budget (the rest wait in a
+FIFO queue and are admitted as others leave; frames a viewer sends before
 admission are rejected).
+
+Overload policy: a frame still waiting on the host ``deadline_ms`` after it
+arrived is dropped (shed) instead of launched: it could no longer be shown in
+time, and launching it would delay every later frame. Both modes keep a
+bounded number of launches in flight, so waiting frames stay on the host where
+the deadline applies.
 
 Two dispatch modes run the same arrival trace:
 
-* ``batched`` (continuous batching): every viewer is pinned to one of
-  ``n_streams`` CUDA streams, so stream order keeps its frames in sequence.
-  Whenever a stream has fewer than ``depth`` launches queued, each of its
-  viewers with a pending frame contributes its oldest one to one persistent
-  batched launch (wrs_push_batch, a CUDA-graph kernel node); frames that
-  arrive while launches run join the next one. Batches on different streams
-  overlap on the device. A launch that would hold a single frame goes out as
-  that viewer's own update (wrs_push_frame, or wrs_push_foveated for rendered
-  frames) instead: a batch of one gains nothing and costs the graph update.
-* ``plain``: every frame is launched on its own (wrs_push_frame) as soon as it
-  arrives, on one stream.
+* ``batched`` (continuous batching): launches go out in arrival order on
+  one CUDA stream (by default; viewers can be spread over ``n_streams``
+  streams, each keeping its viewers' frames in order). Whenever fewer than
+  ``depth`` launches are queued, every viewer with a pending frame
+  contributes its oldest one to one persistent batched launch
+  (wrs_push_batch, a CUDA-graph kernel node); frames that arrive while
+  launches run join the next one. A launch that would hold a single frame
+  goes out as that viewer's own update (wrs_push_frame, or wrs_push_foveated
+  for rendered frames) instead: a batch of one gains nothing and costs the
+  graph update. At light load this is the plain path; when frames queue up,
+  they share launches.
+* ``plain``: every frame is launched on its own (wrs_push_frame), in arrival
+  order, on one stream, with at most ``plain_depth`` launches in flight.
+
+Both modes keep at most ``plain_depth`` frames on the GPU at a time.
 
 A frame's latency is the time from its arrival to the host observing its
 launch's completion event. Results per frame are identical in both modes and
@@ -27,10 +39,10 @@ to a viewer served alone (each viewer's frames are applied in arrival order).
 Frames come from one of two sources: a ``FramePool`` of foveated frames made
 beforehand, or a ``RenderPool`` holding each resolution class's rendered
 image and its mip levels on the device, from which every request's frame is
-foveated on the device for that request's gaze (Sec. 4.3's post-process): in
-plain mode inside the update kernel (wrs_push_foveated), in batched mode by
-one foveation launch per frame into the viewer's frame buffer ahead of the
-batched update. Either way a request carries only a gaze.
+foveated on the device for that request's gaze (Sec. 4.3's post-process)
+inside the update kernel: wrs_push_foveated in plain mode (and for batches of
+one), wrs_push_batch_foveated for batches. Either way a request carries only
+a gaze and no frame is written to memory.
 """
 from __future__ import annotations
 
@@ -42,7 +54,7 @@ import time
 import numpy as np
 import torch
 
-from .wrs import Batch, Foveation, Stream, foveate, make_config, state_bytes
+from .wrs import Batch, Foveation, Stream, make_config, state_bytes
 
 # resolution classes of the mixed-viewer workload: (width, height, ring radii)
 CLASSES = ((3840, 2160, (200.0, 500.0, 1000.0)), (2064, 2208, (200.0, 500.0, 1000.0)),
@@ -70,6 +82,9 @@ class ViewerSpec:
     def state_bytes(self) -> int:
         return state_bytes(make_config(self.width, self.height, self.K, self.radii[0],
                                        color_fp16=self.color_fp16))
+
+    def frame_bytes(self) -> int:
+        return self.pixels * 12  # one RGB float frame (the output, or a staged frame)
 
 
 def viewer_mix(n: int = 64, duration_s: float = 60.0, seed: int = 0,
@@ -158,6 +173,9 @@ class ServeStats:
     viewers_queued_max: int
     peak_state_bytes: int
     single_launches: int = 0  # batched mode: launches that held one frame (the viewer's own kernel)
+    frames_shed: int = 0      # dropped on the host after waiting past the deadline
+    peak_device_bytes: int = 0  # states + outputs (+ frame buffers) of the admitted viewers
+    deadline_ms: float | None = None
 
     def summary(self) -> dict:
         lat = sorted(self.latencies_ms)
@@ -169,27 +187,32 @@ class ServeStats:
 
         return {"mode": self.mode, "duration_s": round(self.duration_s, 2),
                 "frames_served": self.frames_served, "frames_rejected": self.frames_rejected,
+                "frames_shed": self.frames_shed, "deadline_ms": self.deadline_ms,
                 "p50_ms": pct(0.50), "p99_ms": pct(0.99),
                 "mean_ms": round(statistics.mean(lat), 3) if lat else None,
                 "mpx_updates_per_s": round(self.pixel_updates / self.duration_s / 1e6, 1),
                 "launches": self.launches, "frames_per_launch": round(self.frames_served / max(1, self.launches), 2),
                 "single_frame_launches": self.single_launches,
                 "viewers_admitted": self.viewers_admitted, "viewers_queued_max": self.viewers_queued_max,
-                "peak_state_gb": round(self.peak_state_bytes / 1e9, 2)}
+                "peak_state_gb": round(self.peak_state_bytes / 1e9, 2),
+                "peak_device_gb": round(self.peak_device_bytes / 1e9, 2)}
 
 
 class Server:
     """Runs one arrival trace in real time in one of the two dispatch modes."""
 
     def __init__(self, specs, pool: FramePool, budget_bytes: int, mode: str = "batched",
-                 n_streams: int = 2, depth: int = 2, device=None, keep_states: bool = False,
-                 batch_launch=None, single_direct: bool = True):
+                 n_streams: int = 1, depth: int = 12, device=None, keep_states: bool = False,
+                 batch_launch=None, single_direct: bool = True, deadline_ms: float | None = None,
+                 plain_depth: int = 12):
         assert mode in ("batched", "plain")
         self.specs = {v.vid: v for v in specs}
         self.pool = pool
         self.budget = int(budget_bytes)
         self.mode = mode
         self.depth = depth
+        self.plain_depth = plain_depth
+        self.deadline_s = None if deadline_ms is None else deadline_ms * 1e-3
         self.single_direct = single_direct
         self.device = torch.device("cuda") if device is None else torch.device(device)
         self.keep_states = keep_states
@@ -206,17 +229,22 @@ class Server:
                 self.batches.append(b)
         self.init_stream = torch.cuda.Stream(device=self.device)
         self.init_ev = {}         # vid -> event after its state initialisation
-        self.used = 0
+        self.used = 0             # device bytes of the admitted viewers
+        self.used_state = 0       # of which reservoir states
+        self.outs = {}            # vid -> resolved frame of the viewer's latest served frame
         self.live = {}            # vid -> Stream
         self.pushed = collections.defaultdict(list)  # vid -> frame counters pushed, in order
         self.kept = {}            # vid -> Stream kept after leaving (keep_states)
+        self.kept_out = {}        # vid -> its last resolved frame
         self.render = isinstance(pool, RenderPool)
-        self.frame_buf = {}       # vid -> device frame the batched mode foveates into
 
     # -- admission ---------------------------------------------------------
+    def viewer_bytes(self, v: ViewerSpec) -> int:
+        return v.state_bytes() + v.frame_bytes()  # reservoirs + resolved output
+
     def _admit(self, vid) -> bool:
         v = self.specs[vid]
-        need = v.state_bytes()
+        need = self.viewer_bytes(v)
         if self.used + need > self.budget:
             return False
         st = Stream(v.width, v.height, v.K, v.radii[0], seed=v.seed, stream_id=vid,
@@ -226,9 +254,8 @@ class Server:
         self.init_ev[vid] = ev
         self.live[vid] = st
         self.used += need
-        if self.render and self.mode == "batched":
-            self.frame_buf[vid] = torch.empty((v.height, v.width, 3), dtype=torch.float32,
-                                              device=self.device)
+        self.used_state += v.state_bytes()
+        self.outs[vid] = torch.empty((v.height, v.width, 3), dtype=torch.float32, device=self.device)
         return True
 
     def _ready(self, vid, stream):
@@ -239,11 +266,13 @@ class Server:
 
     def _release(self, vid):
         self.init_ev.pop(vid, None)
-        self.frame_buf.pop(vid, None)
         st = self.live.pop(vid)
-        self.used -= self.specs[vid].state_bytes()
+        self.used -= self.viewer_bytes(self.specs[vid])
+        self.used_state -= self.specs[vid].state_bytes()
+        out = self.outs.pop(vid)
         if self.keep_states:
             self.kept[vid] = st
+            self.kept_out[vid] = out
         else:
             st.close()
             del st
@@ -261,8 +290,8 @@ class Server:
         leaving = set()
         inflight = []         # (event, stream index, [(vid, arrival_s)])
         queued = collections.Counter()  # stream index -> launches in flight
-        lat, served, rejected, pix, launches, singles = [], 0, 0, 0, 0, 0
-        admitted_total, queued_max, peak = 0, 0, 0
+        lat, served, rejected, pix, launches, singles, shed = [], 0, 0, 0, 0, 0, 0
+        admitted_total, queued_max, peak, peak_state = 0, 0, 0, 0
         t0 = time.perf_counter()
         while True:
             now = time.perf_counter() - t0
@@ -292,6 +321,7 @@ class Server:
                 waitq.popleft()
                 admitted_total += 1
             peak = max(peak, self.used)
+            peak_state = max(peak_state, self.used_state)
             # arrivals
             while ai < len(trace) and trace[ai][0] <= min(now, duration_s):
                 ta, vid = trace[ai]
@@ -314,14 +344,28 @@ class Server:
                 else:
                     still.append((ev, si, frames))
             inflight = still
+            # overload: frames that waited past the deadline are dropped
+            if self.deadline_s is not None:
+                late = time.perf_counter() - t0 - self.deadline_s
+                for vid in self.live:
+                    q = pending[vid]
+                    while q and q[0] < late:
+                        q.popleft()
+                        shed += 1
             # dispatch
             if self.mode == "batched":
                 for si, stream in enumerate(self.streams):
                     if queued[si] >= self.depth:
                         continue
+                    # at most plain_depth frames on the GPU in either mode: waiting
+                    # frames stay on the host, where the deadline applies
+                    room = self.plain_depth - sum(len(fr) for _, _, fr in inflight)
+                    if room <= 0:
+                        break
                     ready = [vid for vid in self.live
                              if vid % len(self.streams) == si and pending[vid]]
-                    ready = ready[:self.batches[si].max_streams]
+                    ready.sort(key=lambda v: pending[v][0])  # oldest frames first
+                    ready = ready[:min(self.batches[si].max_streams, room)]
                     if not ready:
                         continue
                     if self.single_direct and len(ready) == 1:
@@ -333,9 +377,9 @@ class Server:
                         fr, gz = self.pool.get(self.specs[vid].cls, t)
                         self._ready(vid, stream)
                         if self.render:
-                            self.live[vid].push_foveated(fr, gz, stream=stream)
+                            self.live[vid].push_foveated(fr, gz, out=self.outs[vid], stream=stream)
                         else:
-                            self.live[vid].push_frame(fr, gz, stream=stream)
+                            self.live[vid].push_frame(fr, gz, out=self.outs[vid], stream=stream)
                         busy[vid] += 1
                         self.pushed[vid].append(t)
                         ev = torch.cuda.Event()
@@ -345,26 +389,25 @@ class Server:
                         launches += 1
                         singles += 1
                         continue
-                    sts, frs, gzs, frames = [], [], [], []
+                    sts, frs, gzs, frames, outs = [], [], [], [], []
                     for vid in ready:
                         ta = pending[vid].popleft()
                         t = next_t[vid]
                         next_t[vid] += 1
                         fr, gz = self.pool.get(self.specs[vid].cls, t)
                         self._ready(vid, stream)
-                        if self.render:
-                            # foveate this request's frame on the device first
-                            src, buf = fr, self.frame_buf[vid]
-                            foveate(src.img, src.mip, src.radii, gz, src.filter, out=buf,
-                                    want_ring_map=False, stream=stream)
-                            fr = buf
                         sts.append(self.live[vid])
                         frs.append(fr)
                         gzs.append(gz)
+                        outs.append(self.outs[vid])
                         frames.append((vid, ta))
                         busy[vid] += 1
                         self.pushed[vid].append(t)
-                    self.batches[si].push(sts, frs, gzs, stream=stream)
+                    if self.render:
+                        # each frame foveated on read inside the batched update
+                        self.batches[si].push_foveated(sts, frs, gzs, outs=outs, stream=stream)
+                    else:
+                        self.batches[si].push(sts, frs, gzs, outs=outs, stream=stream)
                     ev = torch.cuda.Event()
                     ev.record(stream)
                     inflight.append((ev, si, frames))
@@ -372,23 +415,30 @@ class Server:
                     launches += 1
             else:
                 stream = self.streams[0]
-                for vid in list(self.live):
-                    while pending[vid]:
-                        ta = pending[vid].popleft()
-                        t = next_t[vid]
-                        next_t[vid] += 1
-                        fr, gz = self.pool.get(self.specs[vid].cls, t)
-                        self._ready(vid, stream)
-                        if self.render:
-                            self.live[vid].push_foveated(fr, gz, stream=stream)
-                        else:
-                            self.live[vid].push_frame(fr, gz, stream=stream)
-                        busy[vid] += 1
-                        ev = torch.cuda.Event()
-                        ev.record(stream)
-                        inflight.append((ev, 0, [(vid, ta)]))
-                        self.pushed[vid].append(t)
-                        launches += 1
+                # oldest frame first, one launch each, at most plain_depth in flight
+                heads = [(pending[vid][0], vid) for vid in self.live if pending[vid]]
+                heads.sort()
+                while heads and queued[0] < self.plain_depth:
+                    _, vid = heads.pop(0)
+                    ta = pending[vid].popleft()
+                    if pending[vid]:
+                        heads.append((pending[vid][0], vid))
+                        heads.sort()
+                    t = next_t[vid]
+                    next_t[vid] += 1
+                    fr, gz = self.pool.get(self.specs[vid].cls, t)
+                    self._ready(vid, stream)
+                    if self.render:
+                        self.live[vid].push_foveated(fr, gz, out=self.outs[vid], stream=stream)
+                    else:
+                        self.live[vid].push_frame(fr, gz, out=self.outs[vid], stream=stream)
+                    busy[vid] += 1
+                    ev = torch.cuda.Event()
+                    ev.record(stream)
+                    inflight.append((ev, 0, [(vid, ta)]))
+                    queued[0] += 1
+                    self.pushed[vid].append(t)
+                    launches += 1
             if now >= duration_s and not inflight and all(not q for q in pending.values()):
                 break
             if not inflight and ai < len(trace) and trace[ai][0] > now + 0.0005:
@@ -398,7 +448,8 @@ class Server:
         for vid in list(self.live):
             self._release(vid)
         return ServeStats(self.mode, max(elapsed, duration_s), served, rejected, pix, lat, launches,
-                          admitted_total, queued_max, peak, singles)
+                          admitted_total, queued_max, peak_state, singles, shed, peak,
+                          None if self.deadline_s is None else round(self.deadline_s * 1e3, 3))
 
     def close(self):
         for b in self.batches:
@@ -407,26 +458,31 @@ class Server:
             st.close()
         self.live.clear()
         self.kept.clear()
+        self.outs.clear()
+        self.kept_out.clear()
 
 
-def replay_alone(spec: ViewerSpec, pushed, pool: FramePool, device=None) -> Stream:
-    """The viewer's frames pushed alone, in the same order, one launch each."""
+def replay_alone(spec: ViewerSpec, pushed, pool: FramePool, device=None):
+    """The viewer's frames pushed alone, in the same order, one launch each;
+    returns the stream and the resolved frame of the last one."""
     st = Stream(spec.width, spec.height, spec.K, spec.radii[0], seed=spec.seed, stream_id=spec.vid,
                 color_fp16=spec.color_fp16, device=device)
+    out = torch.empty((spec.height, spec.width, 3), dtype=torch.float32, device=st.device)
     for t in pushed:
         fr, gz = pool.get(spec.cls, t)
         if isinstance(pool, RenderPool):
-            st.push_foveated(fr, gz)
+            st.push_foveated(fr, gz, out=out)
         else:
-            st.push_frame(fr, gz)
-    return st
+            st.push_frame(fr, gz, out=out)
+    return st, out
 
 
 def serve_compare(n_viewers=64, duration_s=10.0, budget_gb=60.0, seed=0, frames_per_class=8,
                   device=None, rate_hz=(72.0, 120.0), batch_launch=None, classes=CLASSES,
-                  n_streams=4, depth=3, source="frames") -> dict:
+                  n_streams=1, depth=12, source="frames", deadline_ms=20.0) -> dict:
     """Both modes on the same trace; returns their summaries. source: "frames"
-    (foveated beforehand) or "render" (foveated on the device per request)."""
+    (foveated beforehand) or "render" (foveated on the device per request);
+    deadline_ms: frames waiting longer on the host are shed (None: never)."""
     dev = torch.device("cuda") if device is None else torch.device(device)
     specs = viewer_mix(n_viewers, duration_s, seed, rate_hz, classes)
     trace = arrivals(specs, seed)
@@ -436,10 +492,11 @@ def serve_compare(n_viewers=64, duration_s=10.0, budget_gb=60.0, seed=0, frames_
         pool = FramePool(classes, frames_per_class, dev, seed)
     out = {"viewers": n_viewers, "duration_s": duration_s, "budget_gb": budget_gb,
            "rate_hz": list(rate_hz), "frames_offered": len(trace), "source": source,
-           "batched_streams": n_streams, "batched_depth": depth}
+           "batched_streams": n_streams, "batched_depth": depth, "deadline_ms": deadline_ms,
+           "outputs": "every frame resolved into its viewer's output buffer (fused update + resolve)"}
     for mode in ("batched", "plain"):
         srv = Server(specs, pool, int(budget_gb * 1e9), mode=mode, n_streams=n_streams, depth=depth,
-                     device=dev, batch_launch=batch_launch)
+                     device=dev, batch_launch=batch_launch, deadline_ms=deadline_ms)
         out[mode] = srv.run(trace, duration_s).summary()
         srv.close()
         torch.cuda.synchronize(dev)

@@ -11,7 +11,7 @@ import numpy as np
 import torch
 
 from ._lib import (WRS_EMPTY_SLOT, WRS_FILTER_BILINEAR, WRS_FILTER_BOX, WrsConfig, WrsError,
-                   WrsLayout, WrsMipLayout, check, load)
+                   WrsFovSource, WrsLayout, WrsMipLayout, check, load)
 
 
 def _stream_handle(stream) -> int:
@@ -314,6 +314,37 @@ class Batch:
             if tuple(f.shape[-3:]) != (s.height, s.width, 3) or not f.is_contiguous():
                 raise ValueError("frames must be contiguous [H][W][3] float32 tensors")
         check(load().wrs_push_batch(self._b, n, ctxs, fr, gz, fm, ot, _stream_handle(stream)))
+
+    def push_foveated(self, streams, foveations, gazes, fov_maps=None, outs=None, stream=None):
+        """One frame per stream, each foveated on read from its ``Foveation``
+        (image + mip levels on the GPU; all with the same filter) inside the
+        batched update (wrs_push_batch_foveated): the same reservoirs and
+        outputs as Stream.push_foveated of each stream alone."""
+        n = len(streams)
+        if not (len(foveations) == n and len(gazes) == n):
+            raise ValueError("streams, foveations and gazes must have the same length")
+        filters = {FILTERS[f.filter] if isinstance(f.filter, str) else int(f.filter) for f in foveations}
+        if len(filters) != 1:
+            raise ValueError("every foveation source of a batch must use the same filter")
+        srcs = (WrsFovSource * n)()
+        for i, (fv, s) in enumerate(zip(foveations, streams)):
+            if (fv.height, fv.width) != (s.height, s.width):
+                raise ValueError("each foveation source must match its stream's size")
+            iptr, ipitch = _image_args(fv.img, "img")
+            srcs[i].d_img = iptr
+            srcs[i].img_pitch_elems = ipitch
+            srcs[i].d_mip = _dev_ptr(fv.mip, torch.uint8, "mip")
+            srcs[i].mip_bytes = fv.mip.numel()
+            srcs[i].nradii = len(fv.radii)
+            for k, r in enumerate(fv.radii):
+                srcs[i].radii[k] = float(r)
+        ctxs = (C.c_void_p * n)(*[s._ctx.value for s in streams])
+        gz = (C.c_float * (2 * n))(*[float(v) for g in gazes for v in (g[0], g[1])])
+        fm = None if fov_maps is None else (C.c_void_p * n)(
+            *[_dev_ptr(m, torch.uint8, "fov_map") for m in fov_maps])
+        ot = None if outs is None else (C.c_void_p * n)(*[_dev_ptr(o, torch.float32, "out") for o in outs])
+        check(load().wrs_push_batch_foveated(self._b, n, ctxs, srcs, filters.pop(), gz, fm, ot,
+                                             _stream_handle(stream)))
 
     def close(self):
         if self._b:

@@ -1,7 +1,7 @@
 """Summaries of Nsight Compute output for the profiles/ notes.
 
-    python -m paper_2510_03964_gb300.profiling launches <launches.csv>
-    python -m paper_2510_03964_gb300.profiling raw <report.ncu-rep>
+    python profiling.py launches <launches.csv>
+    python profiling.py raw <report.ncu-rep>
 
 ``launches``: per kernel name, the number of launches, total device time and
 share of the listed time (from a ``--metrics gpu__time_duration.sum --csv``

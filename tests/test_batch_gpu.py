@@ -186,3 +186,61 @@ def test_batch_full_temporal_bias_without_outputs():
         assert_bits_equal(mixed[i].export_raw(), solo[i].export_raw(), f"stream {i} state")
     compare_states(mixed[0].export_state(), orc.state(), None, specs[0][3])
     b.close()
+
+
+FOV_MIX = [  # width, height, K, fp16, rule, radii
+    (96, 40, 4, False, 0, (10.0, 25.0)), (128, 32, 8, True, 0, (12.0, 30.0, 60.0)),
+    (64, 16, 3, False, 0, (6.0, 15.0)), (200, 8, 8, False, 0, (20.0, 50.0)),
+    (36, 20, 1, True, 1, (5.0, 12.0)), (256, 12, 16, True, 0, (30.0, 75.0)),
+]
+
+
+@pytest.mark.parametrize("filt", ["box", "bilinear"])
+@pytest.mark.parametrize("with_outs", [True, False])
+def test_foveating_batch_equals_solo_foveated_pushes(filt, with_outs):
+    # each stream's frame foveated on read inside the batched update: the same
+    # reservoirs and outputs as wrs_push_foveated of the stream alone
+    from synth import ground_truth
+    dev = torch.device("cuda")
+    frames = 18
+    fovs, gazes, solo, mixed = [], [], [], []
+    for i, (w, h, K, f16, rule, radii) in enumerate(FOV_MIX):
+        img = torch.from_numpy(ground_truth(w, h, 30 + i)).to(dev)
+        fovs.append(wrs.Foveation(img, radii, filter=filt))
+        gazes.append(gaze_path(w, h, frames, seed=40 + i, model="jitter", jitter_px=w / 3))
+        for lst in (solo, mixed):
+            lst.append(wrs.Stream(w, h, K, radii[0], seed=7 + i, stream_id=i, color_fp16=f16,
+                                  device=dev, update_rule=rule))
+    outs_solo = [torch.empty((h, w, 3), device=dev) for (w, h, *_r) in FOV_MIX]
+    outs_mix = [torch.empty((h, w, 3), device=dev) for (w, h, *_r) in FOV_MIX]
+    b = wrs.Batch(16)
+    for t in range(frames):
+        for i, s in enumerate(solo):
+            s.push_foveated(fovs[i], gazes[i][t], out=outs_solo[i] if with_outs else None)
+        b.push_foveated(mixed, fovs, [g[t] for g in gazes], outs=outs_mix if with_outs else None)
+    torch.cuda.synchronize()
+    for i in range(len(FOV_MIX)):
+        assert mixed[i].check_status() == 0
+        assert mixed[i].frame_index == solo[i].frame_index == frames
+        assert_bits_equal(mixed[i].export_raw(), solo[i].export_raw(), f"stream {i} state")
+        if with_outs:
+            assert_bits_equal(outs_mix[i].cpu().numpy(), outs_solo[i].cpu().numpy(), f"stream {i} out")
+    b.close()
+
+
+def test_foveating_batch_rejects_mixed_filters_and_bad_sources():
+    from synth import ground_truth
+    dev = torch.device("cuda")
+    img = torch.from_numpy(ground_truth(64, 16, 1)).to(dev)
+    a = wrs.Foveation(img, (6.0, 15.0), filter="box")
+    c = wrs.Foveation(img, (6.0, 15.0), filter="bilinear")
+    s1 = wrs.Stream(64, 16, 4, 6.0, seed=1, device=dev)
+    s2 = wrs.Stream(64, 16, 4, 6.0, seed=2, device=dev)
+    b = wrs.Batch(4)
+    with pytest.raises(ValueError):
+        b.push_foveated([s1, s2], [a, c], [(3.0, 4.0), (5.0, 6.0)])
+    small = wrs.Foveation(torch.from_numpy(ground_truth(32, 16, 1)).to(dev), (6.0, 15.0))
+    with pytest.raises(ValueError):
+        b.push_foveated([s1], [small], [(3.0, 4.0)])
+    assert s1.frame_index == s2.frame_index == 0
+    b.close()

@@ -28,18 +28,43 @@ def test_served_viewers_equal_alone(mode, single_direct, source):
                        single_direct=single_direct)
     stats = srv.run(trace, 1.5)
     s = stats.summary()
-    assert stats.frames_served + stats.frames_rejected == len(trace)
+    assert stats.frames_served + stats.frames_rejected + stats.frames_shed == len(trace)
     assert stats.frames_served > 0 and s["p99_ms"] >= s["p50_ms"] > 0
     if mode == "batched":
         assert s["frames_per_launch"] >= 1.0
         if not single_direct:
             assert s["single_frame_launches"] == 0
     for vid, st in srv.kept.items():
-        alone = serve.replay_alone(srv.specs[vid], srv.pushed[vid], pool, device=dev)
+        # the viewer's reservoirs and its last resolved frame, alone and in the mix
+        alone, out = serve.replay_alone(srv.specs[vid], srv.pushed[vid], pool, device=dev)
         torch.cuda.synchronize()
         assert st.frame_index == alone.frame_index == len(srv.pushed[vid])
         assert np.array_equal(st.export_raw(), alone.export_raw()), f"viewer {vid}"
+        if srv.pushed[vid]:
+            assert torch.equal(srv.kept_out[vid].view(torch.int32), out.view(torch.int32)), f"viewer {vid}"
         alone.close()
+    srv.close()
+
+
+@pytest.mark.parametrize("mode", ["batched", "plain"])
+def test_overload_sheds_late_frames_and_bounds_latency(mode):
+    # far more frames than the GPU can take: frames that wait longer than the
+    # deadline are dropped on the host, so the served frames' latency stays
+    # near the deadline instead of growing with the queue
+    dev = torch.device("cuda")
+    big = ((1920, 1080, (120.0, 300.0)),)
+    specs = serve.viewer_mix(24, 1.5, seed=4, rate_hz=(900.0, 900.0), classes=big)
+    trace = serve.arrivals(specs, seed=4)
+    pool = serve.FramePool(big, 4, dev, seed=4)
+    srv = serve.Server(specs, pool, budget_bytes=10**11, mode=mode, device=dev, deadline_ms=10.0,
+                       n_streams=4, depth=3)
+    stats = srv.run(trace, 1.5)
+    s = stats.summary()
+    assert stats.frames_served + stats.frames_rejected + stats.frames_shed == len(trace)
+    assert stats.frames_shed > 0 and stats.frames_served > 0
+    # a served frame waited at most the deadline before its launch, then its
+    # launch and at most the launches queued ahead of it
+    assert s["p99_ms"] < 60.0, s
     srv.close()
 
 
