@@ -126,9 +126,10 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def recorded_traffic(kernel: str, workload_name: str):
+def recorded_traffic(kernel: str, workload_name: str, window: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (matched by hash)."""
+    on the current kernel source (matched by hash) at the same window of
+    stream ages; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -136,7 +137,8 @@ def recorded_traffic(kernel: str, workload_name: str):
         d = json.load(open(path))
         from paper_2510_03964_gb300 import kernel_source_hash
         ent = d.get(workload_name)
-        if ent and ent.get("kernel") == kernel and ent.get("source_hash") == kernel_source_hash():
+        if (ent and ent.get("kernel") == kernel and ent.get("source_hash") == kernel_source_hash()
+                and ent.get("window") == window):
             return ent.get("dram_bytes_per_launch")
     except Exception:
         return None
@@ -738,7 +740,7 @@ def measure_stream(args, dev, spec, seed, world, clocks_rank0: bool, steps: int,
     return res
 
 
-def roofline_line(spec, kernel_avg_ms, rho, peaks, workload_name, kname):
+def roofline_line(spec, kernel_avg_ms, rho, peaks, workload_name, kname, window):
     lit = spec.update_rule == 1
     hw = spec.width * spec.height
     bpp = (algorithmic_bytes_per_px(spec.K, spec.color_fp16, lit)
@@ -746,7 +748,7 @@ def roofline_line(spec, kernel_avg_ms, rho, peaks, workload_name, kname):
     achieved = bpp * hw / (kernel_avg_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
             "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-            "traffic": recorded_traffic(kname, workload_name),
+            "traffic": recorded_traffic(kname, workload_name, window),
             "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs, copy)",
             "algorithmic_bytes_per_px": round(bpp, 2),
             "bytes_rule": f"{algorithmic_bytes_per_px(spec.K, spec.color_fp16, lit)} B read/written "
@@ -872,7 +874,8 @@ def run_ours(args, world, rank, local):
     st_launch = st.get_launch()
     kname = kernel_name(st, spec)
     peaks = measured_peaks()
-    roof = roofline_line(spec, kernel_avg, rho, peaks, args.workload, kname)
+    window = f"stream ages {age}..{age + WINDOW - 1}"
+    roof = roofline_line(spec, kernel_avg, rho, peaks, args.workload, kname, window)
     cfg = workload_config(spec, args.workload)
     pipe_on, pipe_px, pipe_st, pipe_ctas = st_pipe
     blk, px = st_launch
@@ -918,7 +921,8 @@ def run_ours(args, world, rank, local):
                      "roofline": {"frac": roof["frac"], "achieved": roof["achieved"]}},
             "fp16": {"ms_per_frame": round(k16, 4), "replacement_rate": round(m16["rho"], 4),
                      "config_240_frame_mean_ms": (m16["first_pass"] or {}).get("ms_per_frame_1_to_end"),
-                     "roofline": roofline_line(spec16, k16, m16["rho"], peaks, "4k_fp16", kname16)},
+                     "roofline": roofline_line(spec16, k16, m16["rho"], peaks, "4k_fp16", kname16,
+                                               f"stream ages {m16['age']}..{m16['age'] + WINDOW - 1}")},
         }
         if args.cpu_baseline:
             _, err16 = resolve_error_leg(args, dev, spec16, seed, m16)
