@@ -119,7 +119,9 @@ typedef struct {
  * blocks evenly over the CTAs of the persistent kernels. The idx planes of the other blocks therefore lag by up to
  * map_frames - 1 frames between pushes; wrs_export_state folds every pending
  * code first, so exported states always hold complete sample indices, and
- * the ring is not part of an exported or imported state. */
+ * the ring is not part of an exported or imported state. With K <= 2 there
+ * is no ring (map_frames = 0): those kernels are bound by instruction issue
+ * rather than DRAM, so they write each sample index into idx[j] directly. */
 typedef struct {
   int64_t plane_px;
   int64_t plane_bytes4;     /* plane_px * 4 */
@@ -130,7 +132,7 @@ typedef struct {
                                word of the checked build at +16 */
   int64_t W_off, P_off, key_off, idx_off, wt_off, col_off;
   int64_t map_off;          /* ring of replacement-code planes (bytes), 256-byte aligned */
-  int64_t map_frames;       /* planes in the ring (a power of two) */
+  int64_t map_frames;       /* planes in the ring (16), or 0 for K <= 2 */
   int64_t total_bytes;
 } wrs_layout;
 

@@ -224,7 +224,7 @@ __device__ __forceinline__ bool prefetch_fold(const StreamDev& s, const FrameDev
                                               int tid, FoldIn<KM>& in) {
   if constexpr (PX == 1) {
     const int64_t p = p0 + tid;
-    if (s.K <= KM && p < s.hw && folds_now(f, p)) {
+    if (s.K > 2 && s.K <= KM && p < s.hw && folds_now(f, p)) {
       fold_load(s, s.idx, s.K, f.t, p, in);
       return true;
     }

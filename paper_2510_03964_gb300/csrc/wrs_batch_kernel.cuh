@@ -69,14 +69,23 @@ constexpr int kFamF16K48 = 0, kFamF32K48 = 1, kFamAll = 2;
 
 // One tile of entry e: the update from the staged frame, or (FOVF >= 0) from
 // the frame foveated on read.
+// pre: the fold inputs loaded before the wait (for up to 8 slots), or null.
 template <int KT, bool F16, int PX, int T, bool LIT, int FOVF>
 __device__ __forceinline__ int tile(const BatchEntry& e, const StageLayout& L, uint8_t* st,
                                     const float* u, int64_t p0, float d_f, int tid,
-                                    const wrs::FoldFor<KT>* pre = nullptr) {
+                                    const wrs::FoldIn<8>* pre = nullptr) {
+  const wrs::FoldFor<KT>* pk = nullptr;
+  wrs::FoldFor<KT> narrowed;
+  if constexpr (KT > 0 && KT <= 8) {
+    if (pre != nullptr) {
+      narrowed = wrs::narrow_fold<KT>(*pre);
+      pk = &narrowed;
+    }
+  }
   if constexpr (FOVF >= 0)
-    return wrs::compute_tile_fov<KT, F16, PX, T, LIT, FOVF>(e.s, e.f, e.fv, L, st, u, p0, d_f, tid, pre);
+    return wrs::compute_tile_fov<KT, F16, PX, T, LIT, FOVF>(e.s, e.f, e.fv, L, st, u, p0, d_f, tid, pk);
   else
-    return wrs::compute_tile<KT, F16, PX, T, LIT>(e.s, e.f, L, st, u, p0, d_f, tid, pre);
+    return wrs::compute_tile<KT, F16, PX, T, LIT>(e.s, e.f, L, st, u, p0, d_f, tid, pk);
 }
 
 // Warp-specialised like the single-stream pipelined kernel: warp 8 draws each

@@ -446,6 +446,17 @@ __device__ __forceinline__ void store_rgb(float* dst, const float (&o)[N][3]) {
 
 // ---------------------------------------------------------------- sample indices
 
+// With one or two slots the update writes each sample index straight into
+// idx[j] and the state has no code ring: such kernels are bound by
+// instruction issue, not by DRAM, and at their low replacement rates the
+// ring's per-pixel work costs more than the scattered index writes it saves.
+template <int KT>
+__device__ __forceinline__ bool direct_index(const StreamDev& s) {
+  if constexpr (KT == 1 || KT == 2) return true;
+  else if constexpr (KT == 0) return s.K <= 2;
+  else return false;
+}
+
 // Replacement codes: the slot that took the frame's sample (0..K-1), that
 // slot plus kCodeFlush when the history was dropped first (every other slot
 // is then empty), or kCodeKeep when the reservoir kept its samples.
@@ -486,11 +497,24 @@ struct FoldIn {
   uint32_t code[kRingFrames / 4];
 };
 
-// Capacity of the fold inputs of a kernel instantiated for KT slots (0: any K).
+// Capacity of the fold inputs of a kernel instantiated for KT slots (0: any
+// K): exactly KT, so that a kernel for few slots holds no unused registers.
 template <int KT>
 struct FoldCap {
-  static constexpr int value = (KT > 0 && KT <= 8) ? 8 : WRS_MAX_K;
+  static constexpr int value = (KT > 0 && KT <= 8) ? KT : WRS_MAX_K;
 };
+
+// Fold inputs loaded for a larger capacity, narrowed for a kernel of KM slots.
+template <int KM, int KL>
+__device__ __forceinline__ FoldIn<KM> narrow_fold(const FoldIn<KL>& in) {
+  static_assert(KM <= KL, "narrowing only");
+  FoldIn<KM> out;
+#pragma unroll
+  for (int j = 0; j < KM; ++j) out.v[j] = in.v[j];
+#pragma unroll
+  for (int w = 0; w < kRingFrames / 4; ++w) out.code[w] = in.code[w];
+  return out;
+}
 template <int KT>
 using FoldFor = FoldIn<FoldCap<KT>::value>;
 
@@ -798,22 +822,27 @@ __device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f,
         if (kj != kInf) s.key[j * pl + p] = fminf(fmul(kj, kPScale), kFltMax);
       }
     }
+    const bool direct = direct_index<KT>(s);
     if (flush[i]) {
       for (int j = 0; j < K; ++j) {
         if (j == jm[i]) continue;
         s.key[j * pl + p] = kInf;
+        if (direct) s.idx[j * pl + p] = kEmpty;
         store_slot<F16>(s.wt, s.col, K, j, pl, p, 0.0f, 0.0f, 0.0f, 0.0f);
       }
     }
     if (repl[i]) {
       const int j = jm[i];
       s.key[j * pl + p] = ks[i];
+      if (direct) s.idx[j * pl + p] = f.t;
       store_slot<F16>(s.wt, s.col, K, j, pl, p, w[i], rgb[i][0], rgb[i][1], rgb[i][2]);
     }
-    // the sample index goes to the ring as a code
-    const uint8_t code = repl[i] ? static_cast<uint8_t>(jm[i] | (flush[i] ? kCodeFlush : 0u))
-                                 : (flush[i] ? kCodeFlush : kCodeKeep);
-    record_code<KT>(s, f, p, code, PX == 1 ? pre : nullptr);
+    if (!direct) {
+      // the sample index goes to the ring as a code
+      const uint8_t code = repl[i] ? static_cast<uint8_t>(jm[i] | (flush[i] ? kCodeFlush : 0u))
+                                   : (flush[i] ? kCodeFlush : kCodeKeep);
+      record_code<KT>(s, f, p, code, PX == 1 ? pre : nullptr);
+    }
   }
   int replaced = 0;
 #pragma unroll
@@ -829,7 +858,7 @@ __device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f,
 template <bool F16, int PX, bool VEC, bool FOV>
 __device__ __forceinline__ int push_group_literal(const StreamDev& s, const FrameDev& f, int p0,
                                                   const Src& src, float d_f,
-                                                  const FoldFor<1>* pre = nullptr) {
+                                                  const FoldFor<1>* /*pre: unused, no ring*/ = nullptr) {
   const int64_t pl = s.plane;
   const int64_t ss = src.stride;
   const int64_t sa = src.at;
@@ -960,10 +989,10 @@ __device__ __forceinline__ int push_group_literal(const StreamDev& s, const Fram
     if (!valid[i]) continue;
     const int64_t p = p0 + i;
     if (take[i]) {
+      s.idx[p] = f.t;  // one slot: the index is written directly (direct_index)
       store_slot<F16>(s.wt, s.col, 1, 0, pl, p, w[i], rgb[i][0], rgb[i][1], rgb[i][2]);
       taken += 1;
     }
-    record_code<1>(s, f, p, take[i] ? static_cast<uint8_t>(0) : kCodeKeep, PX == 1 ? pre : nullptr);
   }
   return taken;
 }

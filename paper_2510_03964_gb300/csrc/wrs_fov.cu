@@ -185,10 +185,7 @@ __global__ void __launch_bounds__(kFovThreads) foveate4_kernel(FovArgs a) {
     const int32_t y = (int32_t)(q / wq);
     const int32_t x0 = 4 * (int32_t)(q - (int64_t)y * wq);
     float rgb[12];
-    uint32_t lv = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      lv |= (uint32_t)wrs::fov_pixel<FILTER>(a.fv, a.gx, a.gy, x0 + i, y, rgb + 3 * i) << (8 * i);
+    const uint32_t lv = wrs::fov_quad<FILTER>(a.fv, a.gx, a.gy, x0, y, rgb);
     float4* o = reinterpret_cast<float4*>(a.frame + (int64_t)y * a.frame_pitch + 3 * (int64_t)x0);
     o[0] = make_float4(rgb[0], rgb[1], rgb[2], rgb[3]);
     o[1] = make_float4(rgb[4], rgb[5], rgb[6], rgb[7]);

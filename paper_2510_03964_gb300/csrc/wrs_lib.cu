@@ -98,10 +98,11 @@ void wrs_make_layout(const wrs_config* c, wrs_layout* L) {
     L->wt_off = -1;
     L->col_off = L->idx_off + c->K * L->plane_bytes4;
   }
-  // one code byte per pixel and frame for the last kMapFrames frames
+  // one code byte per pixel and frame for the last kMapFrames frames; none
+  // for one or two slots, whose kernels write the sample indices directly
   L->map_off = L->col_off + c->K * L->plane_bytes_col;
-  L->map_frames = kMapFrames;
-  L->total_bytes = L->map_off + kMapFrames * pl;
+  L->map_frames = c->K <= 2 ? 0 : kMapFrames;
+  L->total_bytes = L->map_off + L->map_frames * pl;
 }
 
 float wrs_delta(const wrs_config* c) {
@@ -134,12 +135,14 @@ StreamDev wrs_stream_dev(const wrs_ctx* x) {
   s.bias = x->cfg.temporal_bias;
   s.literal = x->cfg.update_rule == WRS_RULE_LITERAL ? 1 : 0;
   s.replacements = reinterpret_cast<unsigned long long*>(x->state + x->lay.status_off + 8);
-  s.maps = x->state + x->lay.map_off;  // the ring stays in the primary buffer
+  // the ring stays in the primary buffer (none for one or two slots)
+  s.maps = x->lay.map_frames > 0 ? x->state + x->lay.map_off : nullptr;
   s.check = reinterpret_cast<uint32_t*>(x->state + x->lay.status_off + 16);
   return s;
 }
 
 uint32_t wrs_map_lo(const wrs_ctx* x) {
+  if (x->lay.map_frames == 0) return x->t;  // no ring: nothing to fold
   const uint32_t back = static_cast<uint32_t>(x->lay.map_frames - 1);
   const uint32_t oldest = x->t >= back ? x->t - back : 0u;  // oldest frame the ring still holds
   return x->base > oldest ? x->base : oldest;
@@ -349,6 +352,7 @@ cudaError_t wrs_launch_push(const StreamDev& s, const FrameDev& f, int block, in
 }
 
 cudaError_t wrs_fold_all(wrs_ctx* x, cudaStream_t st) {
+  if (x->lay.map_frames == 0) x->base = x->t;  // indices written directly
   if (x->base == x->t) return cudaSuccess;
   const StreamDev s = wrs_stream_dev(x);
   fold_all_kernel<<<static_cast<unsigned>(x->sms) * 8, 256, 0, st>>>(s, x->base, x->t);

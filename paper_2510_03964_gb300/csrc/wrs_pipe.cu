@@ -49,8 +49,16 @@ constexpr int kPipeThreads = (kConsumerWarps + 1) * 32;
 // only at the per-stage full/empty barriers, never at a block-wide barrier.
 // FOVF >= 0: the frame is not copied but foveated by the consumers from `fv`
 // with filter FOVF (WRS_FILTER_*) as they compute; FOVF < 0: `fv` is unused.
+// Resident CTAs per SM the compiler is asked to fit: three for one or two
+// slots (their stages are small, and the extra warps hide the per-pixel
+// arithmetic's latency), two for one pixel per thread, else one.
+template <int KT, int PX>
+constexpr int pipe_min_blocks() {
+  return PX != 1 ? 1 : ((KT == 1 || KT == 2) ? 3 : 2);
+}
+
 template <int KT, bool F16, int PX, bool LIT, int FOVF = -1>
-__global__ void __launch_bounds__(kPipeThreads, PX == 1 ? 2 : 1)
+__global__ void __launch_bounds__(kPipeThreads, pipe_min_blocks<KT, PX>())
     pipe_kernel(const __grid_constant__ StreamDev s, const __grid_constant__ FrameDev f,
                 const PipeArgs a, const __grid_constant__ FovDev fv) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -95,7 +103,7 @@ __global__ void __launch_bounds__(kPipeThreads, PX == 1 ? 2 : 1)
         r, my_tiles, a.timeout_ns, lane,
         [&](int it) {
           const int64_t p0 = static_cast<int64_t>(first + it * step) * T;
-          if constexpr (KT > 0) folding = wrs::prefetch_fold<wrs::FoldCap<KT>::value, PX>(s, f, p0, tid, fin);
+          if constexpr (KT > 2) folding = wrs::prefetch_fold<wrs::FoldCap<KT>::value, PX>(s, f, p0, tid, fin);
         },
         [&](int it, uint8_t* st, const float* u) {
           const int64_t p0 = static_cast<int64_t>(first + it * step) * T;

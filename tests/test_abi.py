@@ -55,6 +55,10 @@ def test_state_bytes_and_layout(lib):
     # odd K: the weight planes end off a 256-byte boundary and the records start on the next
     lay3 = pkg.state_layout(pkg.make_config(8, 8, 3, 2.0, color_fp16=True))
     assert lay3.col_off == (lay3.wt_off + 3 * 2 * lay3.plane_px + 255) // 256 * 256
+    # one or two slots: the sample indices are written directly, no code ring
+    lay1 = pkg.state_layout(pkg.make_config(64, 8, 1, 4.0))
+    assert lay1.map_frames == 0 and lay1.total_bytes == lay1.map_off
+    assert pkg.state_layout(pkg.make_config(64, 8, 3, 4.0)).map_frames == 16
     # ragged size: planes padded to 64 entries
     lay2 = pkg.state_layout(pkg.make_config(37, 23, 3, 5.0))
     assert lay2.plane_px == 896

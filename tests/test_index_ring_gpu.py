@@ -27,6 +27,9 @@ def _flush_map(w, h, t):
     ((300, 70), 8, True, None),
     ((300, 70), 4, False, (False, 0, 0, 0)),     # plain kernel, 4 pixels per thread
     ((301, 67), 3, False, None),                 # odd width: plain kernel, generic K
+    ((300, 70), 1, False, None),                 # one or two slots: indices written
+    ((300, 70), 2, True, None),                  # directly, no ring
+    ((301, 67), 2, False, (False, 0, 0, 0)),
 ])
 def test_exports_at_any_frame_match_the_oracle(shape, K, fp16, pipeline):
     w, h = shape
