@@ -188,11 +188,11 @@ __device__ __forceinline__ void draw_tile_uniforms_warp(const StreamDev& s, cons
 // Computes consumer thread `tid`'s PX pixels of a landed tile from shared
 // memory; returns how many of them replaced a slot. LIT: the literal n = 1
 // rule (KT = 1).
-template <int KT, bool F16, int PX, int T, bool LIT = false>
+template <int KT, bool F16, int PX, int T, bool LIT = false, int KM = FoldCap<KT>::value>
 __device__ __forceinline__ int compute_tile(const StreamDev& s, const FrameDev& f,
                                             const StageLayout& L, const uint8_t* st,
                                             const float* u, int64_t p0, float d_f, int tid,
-                                            const FoldFor<KT>* pre = nullptr) {
+                                            const FoldIn<KM>* pre = nullptr) {
   const int tl = tid * PX;
   const int64_t p = p0 + tl;
   if (p >= s.hw) return 0;
@@ -207,11 +207,11 @@ __device__ __forceinline__ int compute_tile(const StreamDev& s, const FrameDev& 
   src.frame = reinterpret_cast<const float*>(st + L.frame) + 3 * tl;
   src.u = u + tl;
   if constexpr (LIT) {
-    if (f.fov != nullptr) return push_group_literal<F16, PX, true, true>(s, f, static_cast<int>(p), src, d_f, pre);
-    return push_group_literal<F16, PX, true, false>(s, f, static_cast<int>(p), src, d_f, pre);
+    if (f.fov != nullptr) return push_group_literal<F16, PX, true, true>(s, f, static_cast<int>(p), src, d_f);
+    return push_group_literal<F16, PX, true, false>(s, f, static_cast<int>(p), src, d_f);
   } else {
-    if (f.fov != nullptr) return push_group<KT, F16, PX, true, true>(s, f, static_cast<int>(p), src, d_f, pre);
-    return push_group<KT, F16, PX, true, false>(s, f, static_cast<int>(p), src, d_f, pre);
+    if (f.fov != nullptr) return push_group<KT, F16, PX, true, true, KM>(s, f, static_cast<int>(p), src, d_f, pre);
+    return push_group<KT, F16, PX, true, false, KM>(s, f, static_cast<int>(p), src, d_f, pre);
   }
 }
 
@@ -236,12 +236,12 @@ __device__ __forceinline__ bool prefetch_fold(const StreamDev& s, const FrameDev
 // As compute_tile, with the thread's PX pixels of the frame foveated from
 // `fv` into the stage's frame segment first (the producer copied no frame);
 // each thread writes and then reads only its own pixels there.
-template <int KT, bool F16, int PX, int T, bool LIT, int FILTER>
+template <int KT, bool F16, int PX, int T, bool LIT, int FILTER, int KM = FoldCap<KT>::value>
 __device__ __forceinline__ int compute_tile_fov(const StreamDev& s, const FrameDev& f,
                                                 const FovDev& fv, const StageLayout& L,
                                                 uint8_t* st, const float* u, int64_t p0,
                                                 float d_f, int tid,
-                                                const FoldFor<KT>* pre = nullptr) {
+                                                const FoldIn<KM>* pre = nullptr) {
   const int tl = tid * PX;
   const int64_t p = p0 + tl;
   if (p >= s.hw) return 0;
@@ -250,7 +250,7 @@ __device__ __forceinline__ int compute_tile_fov(const StreamDev& s, const FrameD
   float* fr = reinterpret_cast<float*>(st + L.frame) + 3 * tl;
 #pragma unroll
   for (int i = 0; i < PX; ++i) fov_pixel<FILTER>(fv, f.gx, f.gy, x + i, y, fr + 3 * i);
-  return compute_tile<KT, F16, PX, T, LIT>(s, f, L, st, u, p0, d_f, tid, pre);
+  return compute_tile<KT, F16, PX, T, LIT, KM>(s, f, L, st, u, p0, d_f, tid, pre);
 }
 
 __device__ __forceinline__ void add_warp_count(unsigned long long* total, int count, int lane) {

@@ -62,6 +62,15 @@ __device__ __forceinline__ bool entry_f16(const BatchEntry& e) {
 constexpr int kConsumerWarps = 8;
 constexpr int kBatchThreads = (kConsumerWarps + 1) * 32;
 
+// Adds a warp's running count of replacements in entry ei to the CTA's
+// per-stream total and clears it: once per stream a warp leaves, not per tile.
+__device__ __forceinline__ void flush_count(unsigned long long* replaced_s, int ei, int& count,
+                                            int lane) {
+  const unsigned c = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(count));
+  if (lane == 0 && c != 0) atomicAdd(&replaced_s[ei], static_cast<unsigned long long>(c));
+  count = 0;
+}
+
 // Arithmetic families: a batch whose streams all use FP16 colour with K = 4
 // or 8 (the serving mix) or all FP32 colour with K = 4 or 8 gets a kernel
 // holding only those two variants; any other mix gets the kernel with all.
@@ -69,23 +78,39 @@ constexpr int kFamF16K48 = 0, kFamF32K48 = 1, kFamAll = 2;
 
 // One tile of entry e: the update from the staged frame, or (FOVF >= 0) from
 // the frame foveated on read.
-// pre: the fold inputs loaded before the wait (for up to 8 slots), or null.
+// pre: the fold inputs loaded before the wait (for up to 8 slots, used as
+// they are: no narrowed copy, which would have to live in local memory), or
+// null. The generic-K and literal forms take none.
 template <int KT, bool F16, int PX, int T, bool LIT, int FOVF>
 __device__ __forceinline__ int tile(const BatchEntry& e, const StageLayout& L, uint8_t* st,
                                     const float* u, int64_t p0, float d_f, int tid,
                                     const wrs::FoldIn<8>* pre = nullptr) {
-  const wrs::FoldFor<KT>* pk = nullptr;
-  wrs::FoldFor<KT> narrowed;
-  if constexpr (KT > 0 && KT <= 8) {
-    if (pre != nullptr) {
-      narrowed = wrs::narrow_fold<KT>(*pre);
-      pk = &narrowed;
-    }
+  if constexpr (KT == 4 || KT == 8) {
+    if constexpr (FOVF >= 0)
+      return wrs::compute_tile_fov<KT, F16, PX, T, LIT, FOVF, 8>(e.s, e.f, e.fv, L, st, u, p0, d_f, tid, pre);
+    else
+      return wrs::compute_tile<KT, F16, PX, T, LIT, 8>(e.s, e.f, L, st, u, p0, d_f, tid, pre);
+  } else {
+    if constexpr (FOVF >= 0)
+      return wrs::compute_tile_fov<KT, F16, PX, T, LIT, FOVF>(e.s, e.f, e.fv, L, st, u, p0, d_f, tid);
+    else
+      return wrs::compute_tile<KT, F16, PX, T, LIT>(e.s, e.f, L, st, u, p0, d_f, tid);
   }
-  if constexpr (FOVF >= 0)
-    return wrs::compute_tile_fov<KT, F16, PX, T, LIT, FOVF>(e.s, e.f, e.fv, L, st, u, p0, d_f, tid, pk);
-  else
-    return wrs::compute_tile<KT, F16, PX, T, LIT>(e.s, e.f, L, st, u, p0, d_f, tid, pk);
+}
+
+// The producer's work for one tile of entry e: its uniforms, then its bulk
+// copies. KT, CS > 0 fix the slot count and colour bytes at compile time (the
+// K = 4 / 8 families), so the copy sizes and stage offsets fold to constants.
+template <int T, int KT, int CS, bool COPY_FRAME>
+__device__ __forceinline__ void produce_tile(const BatchEntry& e, int64_t p0, uint8_t* st, float* u,
+                                             uint64_t* full, int ln, uint32_t stage_cap) {
+  const int K = KT > 0 ? KT : e.s.K;
+  const int cs = CS > 0 ? CS : (entry_f16(e) ? 2 : 4);
+  const bool resolve = stage_records(e);
+  const StageLayout L = wrs::stage_layout(T, K, cs, resolve);
+  wrs::draw_tile_uniforms_warp<T>(e.s, e.f, p0, u, ln);
+  __syncwarp();
+  wrs::issue_tile_copies<T>(e.s, e.f, K, cs, resolve, L, st, full, p0, 0u, ln, COPY_FRAME, stage_cap);
 }
 
 // Warp-specialised like the single-stream pipelined kernel: warp 8 draws each
@@ -127,26 +152,34 @@ __global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
                             pe = entry_after(a, g, pe);
                             const BatchEntry& e = a.e[pe];
                             const int64_t p0 = static_cast<int64_t>(g - e.tile0) * T;
-                            const int cs = entry_f16(e) ? 2 : 4;
-                            const bool resolve = stage_records(e);
-                            const StageLayout L = wrs::stage_layout(T, e.s.K, cs, resolve);
-                            wrs::draw_tile_uniforms_warp<T>(e.s, e.f, p0, u, ln);
-                            __syncwarp();
-                            wrs::issue_tile_copies<T>(e.s, e.f, e.s.K, cs, resolve, L, st, full,
-                                                      p0, 0u, ln, FOVF < 0, r.stage_bytes);
+                            constexpr bool cf = FOVF < 0;
+                            if constexpr (FAM == kFamF16K48) {
+                              if (e.code == 0) produce_tile<T, 4, 2, cf>(e, p0, st, u, full, ln, r.stage_bytes);
+                              else produce_tile<T, 8, 2, cf>(e, p0, st, u, full, ln, r.stage_bytes);
+                            } else if constexpr (FAM == kFamF32K48) {
+                              if (e.code == 2) produce_tile<T, 4, 4, cf>(e, p0, st, u, full, ln, r.stage_bytes);
+                              else produce_tile<T, 8, 4, cf>(e, p0, st, u, full, ln, r.stage_bytes);
+                            } else {
+                              produce_tile<T, 0, 0, cf>(e, p0, st, u, full, ln, r.stage_bytes);
+                            }
                           });
   } else {
-    // fold inputs of entries that compute with K = 4 or 8 (or the literal
-    // rule), loaded before the wait; the generic-K arithmetic loads its own
+    // fold inputs of entries that compute with K = 4 or 8, loaded before the
+    // wait; the generic-K arithmetic loads its own (the literal rule has none)
     wrs::FoldIn<8> fin;
     bool folding = false;
-    int ei = 0;  // entry of the consumer's current tile
+    int ei = 0;        // entry of the consumer's current tile
+    int replaced = 0;  // this thread's replacements in entry ei so far
     wrs::consume(r, my_tiles, a.timeout_ns, lane, [&](int it) {
       const int g = first + it * step;
-      ei = entry_after(a, g, ei);
+      const int next = entry_after(a, g, ei);
+      if (next != ei) {
+        flush_count(replaced_s, ei, replaced, lane);
+        ei = next;
+      }
       const BatchEntry& e = a.e[ei];
       const int64_t p0 = static_cast<int64_t>(g - e.tile0) * T;
-      folding = (e.code < 4 || e.code > 5) && wrs::prefetch_fold<8, PX>(e.s, e.f, p0, tid, fin);
+      folding = e.code < 4 && wrs::prefetch_fold<8, PX>(e.s, e.f, p0, tid, fin);
     }, [&](int it, uint8_t* st, const float* u) {
       const int g = first + it * step;
       const BatchEntry& e = a.e[ei];
@@ -176,9 +209,9 @@ __global__ void __launch_bounds__(kBatchThreads, PX == 1 ? 2 : 1)
         default: rc = tile<0, false, PX, T, false, FOVF>(e, wrs::stage_layout(T, e.s.K, 4, resolve), st, u, p0, d_f, tid); break;
         }
       }
-      const unsigned c = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(rc));
-      if (lane == 0 && c != 0) atomicAdd(&replaced_s[ei], static_cast<unsigned long long>(c));
+      replaced += rc;
     });
+    flush_count(replaced_s, ei, replaced, lane);
   }
   __syncthreads();
   if (tid < a.n && replaced_s[tid] != 0) atomicAdd(a.e[tid].s.replacements, replaced_s[tid]);

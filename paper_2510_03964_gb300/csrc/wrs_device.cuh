@@ -504,17 +504,6 @@ struct FoldCap {
   static constexpr int value = (KT > 0 && KT <= 8) ? KT : WRS_MAX_K;
 };
 
-// Fold inputs loaded for a larger capacity, narrowed for a kernel of KM slots.
-template <int KM, int KL>
-__device__ __forceinline__ FoldIn<KM> narrow_fold(const FoldIn<KL>& in) {
-  static_assert(KM <= KL, "narrowing only");
-  FoldIn<KM> out;
-#pragma unroll
-  for (int j = 0; j < KM; ++j) out.v[j] = in.v[j];
-#pragma unroll
-  for (int w = 0; w < kRingFrames / 4; ++w) out.code[w] = in.code[w];
-  return out;
-}
 template <int KT>
 using FoldFor = FoldIn<FoldCap<KT>::value>;
 
@@ -569,10 +558,12 @@ __device__ __forceinline__ void fold_store(const StreamDev& s, uint32_t* idx, in
 
 // This frame's code of pixel p into the ring and, for the band this frame
 // folds, every pending code into the idx planes (from `pre` when the fold's
-// inputs were loaded ahead, else loaded here).
-template <int KT>
+// inputs were loaded ahead, else loaded here). KM >= K: the capacity of the
+// preloaded inputs (a batched kernel loads for up to 8 slots whatever the
+// stream's K; entries past K are dead code once K is a constant).
+template <int KT, int KM = FoldCap<KT>::value>
 __device__ __forceinline__ void record_code(const StreamDev& s, const FrameDev& f, int64_t p,
-                                            uint8_t c, const FoldFor<KT>* pre) {
+                                            uint8_t c, const FoldIn<KM>* pre) {
   const int K = KT > 0 ? KT : s.K;
   s.maps[static_cast<int64_t>(f.t & kRingMask) * s.plane + p] = c;
   if (!folds_now(f, p)) return;
@@ -627,10 +618,10 @@ __device__ __forceinline__ bool group_in_bounds(const StreamDev& s, const FrameD
 // every pixel is addressed on its own (and may lie past the end of the image).
 // FOV: a flush map is present (f.fov != null); without one the flush logic is
 // compiled out.
-template <int KT, bool F16, int PX, bool VEC, bool FOV>
+template <int KT, bool F16, int PX, bool VEC, bool FOV, int KM = FoldCap<KT>::value>
 __device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f, int p0,
                                           const Src& src, float d_f,
-                                          const FoldFor<KT>* pre = nullptr) {
+                                          const FoldIn<KM>* pre = nullptr) {
   const int K = KT > 0 ? KT : s.K;
   const int64_t pl = s.plane;
   const int64_t ss = src.stride;
@@ -841,7 +832,7 @@ __device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f,
       // the sample index goes to the ring as a code
       const uint8_t code = repl[i] ? static_cast<uint8_t>(jm[i] | (flush[i] ? kCodeFlush : 0u))
                                    : (flush[i] ? kCodeFlush : kCodeKeep);
-      record_code<KT>(s, f, p, code, PX == 1 ? pre : nullptr);
+      record_code<KT, KM>(s, f, p, code, PX == 1 ? pre : nullptr);
     }
   }
   int replaced = 0;
@@ -857,8 +848,7 @@ __device__ __forceinline__ int push_group(const StreamDev& s, const FrameDev& f,
 // resolve and store code as the key race.
 template <bool F16, int PX, bool VEC, bool FOV>
 __device__ __forceinline__ int push_group_literal(const StreamDev& s, const FrameDev& f, int p0,
-                                                  const Src& src, float d_f,
-                                                  const FoldFor<1>* /*pre: unused, no ring*/ = nullptr) {
+                                                  const Src& src, float d_f) {
   const int64_t pl = s.plane;
   const int64_t ss = src.stride;
   const int64_t sa = src.at;
