@@ -8,6 +8,14 @@ while their device bytes (reservoir state and output) fit under an HBM budget (t
 FIFO queue and are admitted as others leave; frames a viewer sends before
 admission are rejected).
 
+Parking (``park_idle_ms``): when a joining viewer does not fit the budget,
+admitted viewers with nothing pending or in flight for at least that long are
+moved to host memory, least recently active first: their reservoirs through
+wrs_export_state and their last resolved frame, freeing their device bytes.
+A parked viewer stays admitted; when its next frame is due it is restored
+through wrs_import_state (parking other idle viewers if it must) and carries
+on bit for bit as if it had stayed resident.
+
 Overload policy: a frame still waiting on the host ``deadline_ms`` after it
 arrived is dropped (shed) instead of launched: it could no longer be shown in
 time, and launching it would delay every later frame. Both modes keep a
@@ -176,6 +184,8 @@ class ServeStats:
     frames_shed: int = 0      # dropped on the host after waiting past the deadline
     peak_device_bytes: int = 0  # states + outputs (+ frame buffers) of the admitted viewers
     deadline_ms: float | None = None
+    parks: int = 0              # viewers moved to host memory (wrs_export_state)
+    restores: int = 0           # parked viewers brought back (wrs_import_state)
 
     def summary(self) -> dict:
         lat = sorted(self.latencies_ms)
@@ -194,6 +204,7 @@ class ServeStats:
                 "launches": self.launches, "frames_per_launch": round(self.frames_served / max(1, self.launches), 2),
                 "single_frame_launches": self.single_launches,
                 "viewers_admitted": self.viewers_admitted, "viewers_queued_max": self.viewers_queued_max,
+                "viewers_parked": self.parks, "viewers_restored": self.restores,
                 "peak_state_gb": round(self.peak_state_bytes / 1e9, 2),
                 "peak_device_gb": round(self.peak_device_bytes / 1e9, 2)}
 
@@ -204,7 +215,7 @@ class Server:
     def __init__(self, specs, pool: FramePool, budget_bytes: int, mode: str = "batched",
                  n_streams: int = 1, depth: int = 12, device=None, keep_states: bool = False,
                  batch_launch=None, single_direct: bool = True, deadline_ms: float | None = None,
-                 plain_depth: int = 12):
+                 plain_depth: int = 12, park_idle_ms: float | None = None):
         assert mode in ("batched", "plain")
         self.specs = {v.vid: v for v in specs}
         self.pool = pool
@@ -213,6 +224,10 @@ class Server:
         self.depth = depth
         self.plain_depth = plain_depth
         self.deadline_s = None if deadline_ms is None else deadline_ms * 1e-3
+        self.park_idle_s = None if park_idle_ms is None else park_idle_ms * 1e-3
+        self.parked = {}          # vid -> (state bytes, frame index, last resolved frame), on the host
+        self.parks = 0
+        self.restores = 0
         self.single_direct = single_direct
         self.device = torch.device("cuda") if device is None else torch.device(device)
         self.keep_states = keep_states
@@ -258,6 +273,66 @@ class Server:
         self.outs[vid] = torch.empty((v.height, v.width, 3), dtype=torch.float32, device=self.device)
         return True
 
+    def _stream_of(self, vid):
+        return self.streams[vid % len(self.streams)]
+
+    def _park(self, vid):
+        # an idle viewer's reservoirs and last resolved frame to host memory
+        stream = self._stream_of(vid)
+        ev = self.init_ev.pop(vid, None)
+        if ev is not None:
+            stream.wait_event(ev)
+        st = self.live.pop(vid)
+        buf = st.export_raw(stream=stream)  # waits for its copies
+        out = self.outs.pop(vid)
+        with torch.cuda.stream(stream):
+            host_out = out.to("cpu")
+        self.parked[vid] = (buf, st.frame_index, host_out)
+        st.close()
+        v = self.specs[vid]
+        self.used -= self.viewer_bytes(v)
+        self.used_state -= v.state_bytes()
+        self.parks += 1
+
+    def _restore(self, vid):
+        v = self.specs[vid]
+        stream = self._stream_of(vid)
+        buf, t, host_out = self.parked.pop(vid)
+        st = Stream(v.width, v.height, v.K, v.radii[0], seed=v.seed, stream_id=vid,
+                    color_fp16=v.color_fp16, device=self.device, stream=stream)
+        st.import_raw(buf, t, stream=stream)
+        with torch.cuda.stream(stream):
+            self.outs[vid] = host_out.to(self.device)
+        self.live[vid] = st
+        self.used += self.viewer_bytes(v)
+        self.used_state += v.state_bytes()
+        self.restores += 1
+
+    def _make_room(self, need, exclude, idle_since):
+        # parks admitted viewers that are idle (nothing pending or in flight,
+        # last active at or before idle_since), least recently active first,
+        # until `need` more bytes fit the budget; True if they do
+        cands = sorted((self._last[vid], vid) for vid in self.live
+                       if vid not in exclude and self._busy[vid] == 0 and not self._pending[vid]
+                       and vid not in self._leaving and self._last[vid] <= idle_since)
+        for _, vid in cands:
+            if self.used + need <= self.budget:
+                break
+            self._park(vid)
+        return self.used + need <= self.budget
+
+    def _keep_parked(self, vid):
+        # a parked viewer that leaves: its state back on the device for the
+        # caller (keep_states), outside the budget
+        buf, t, host_out = self.parked.pop(vid)
+        if self.keep_states:
+            v = self.specs[vid]
+            st = Stream(v.width, v.height, v.K, v.radii[0], seed=v.seed, stream_id=vid,
+                        color_fp16=v.color_fp16, device=self.device)
+            st.import_raw(buf, t)
+            self.kept[vid] = st
+            self.kept_out[vid] = host_out.to(self.device)
+
     def _ready(self, vid, stream):
         # a launch that touches a newly admitted viewer waits for its initialisation
         ev = self.init_ev.pop(vid, None)
@@ -288,6 +363,8 @@ class Server:
         next_t = collections.defaultdict(int)                 # vid -> next frame counter
         busy = collections.Counter()  # vid -> frames in flight
         leaving = set()
+        last = collections.defaultdict(float)  # vid -> last arrival or completion (s)
+        self._busy, self._pending, self._leaving, self._last = busy, pending, leaving, last
         inflight = []         # (event, stream index, [(vid, arrival_s)])
         queued = collections.Counter()  # stream index -> launches in flight
         lat, served, rejected, pix, launches, singles, shed = [], 0, 0, 0, 0, 0, 0
@@ -299,7 +376,10 @@ class Server:
             while ji < len(joins) and joins[ji][0] <= now:
                 vid = joins[ji][1]
                 ji += 1
-                if self._admit(vid):
+                last[vid] = now
+                if not waitq and self.park_idle_s is not None:
+                    self._make_room(self.viewer_bytes(self.specs[vid]), {vid}, now - self.park_idle_s)
+                if not waitq and self._admit(vid):
                     admitted_total += 1
                 else:
                     waitq.append(vid)
@@ -315,8 +395,13 @@ class Server:
                 elif vid in self.live and busy[vid] == 0 and not pending[vid]:
                     self._release(vid)
                     leaving.discard(vid)
-                elif vid not in self.live and vid not in waitq:
+                elif vid in self.parked and not pending[vid]:
+                    self._keep_parked(vid)
                     leaving.discard(vid)
+                elif vid not in self.live and vid not in self.parked and vid not in waitq:
+                    leaving.discard(vid)
+            if waitq and self.park_idle_s is not None:
+                self._make_room(self.viewer_bytes(self.specs[waitq[0]]), {waitq[0]}, now - self.park_idle_s)
             while waitq and self._admit(waitq[0]):
                 waitq.popleft()
                 admitted_total += 1
@@ -326,8 +411,9 @@ class Server:
             while ai < len(trace) and trace[ai][0] <= min(now, duration_s):
                 ta, vid = trace[ai]
                 ai += 1
-                if vid in self.live and vid not in leaving:
+                if (vid in self.live or vid in self.parked) and vid not in leaving:
                     pending[vid].append(ta)
+                    last[vid] = max(last[vid], ta)
                 else:
                     rejected += 1
             # completions
@@ -338,6 +424,7 @@ class Server:
                     queued[si] -= 1
                     for vid, ta in frames:
                         lat.append((done_now - ta) * 1e3)
+                        last[vid] = done_now
                         busy[vid] -= 1
                         served += 1
                         pix += self.specs[vid].pixels
@@ -347,11 +434,18 @@ class Server:
             # overload: frames that waited past the deadline are dropped
             if self.deadline_s is not None:
                 late = time.perf_counter() - t0 - self.deadline_s
-                for vid in self.live:
+                for vid in list(self.live) + list(self.parked):
                     q = pending[vid]
                     while q and q[0] < late:
                         q.popleft()
                         shed += 1
+            # parked viewers with a frame due come back, oldest frame first
+            if self.parked:
+                due = sorted((pending[vid][0], vid) for vid in self.parked if pending[vid])
+                for _, vid in due:
+                    need = self.viewer_bytes(self.specs[vid])
+                    if self.used + need <= self.budget or self._make_room(need, {vid}, now):
+                        self._restore(vid)
             # dispatch
             if self.mode == "batched":
                 for si, stream in enumerate(self.streams):
@@ -447,9 +541,12 @@ class Server:
         elapsed = time.perf_counter() - t0
         for vid in list(self.live):
             self._release(vid)
+        for vid in list(self.parked):
+            self._keep_parked(vid)
         return ServeStats(self.mode, max(elapsed, duration_s), served, rejected, pix, lat, launches,
                           admitted_total, queued_max, peak_state, singles, shed, peak,
-                          None if self.deadline_s is None else round(self.deadline_s * 1e3, 3))
+                          None if self.deadline_s is None else round(self.deadline_s * 1e3, 3),
+                          self.parks, self.restores)
 
     def close(self):
         for b in self.batches:
@@ -479,10 +576,12 @@ def replay_alone(spec: ViewerSpec, pushed, pool: FramePool, device=None):
 
 def serve_compare(n_viewers=64, duration_s=10.0, budget_gb=60.0, seed=0, frames_per_class=8,
                   device=None, rate_hz=(72.0, 120.0), batch_launch=None, classes=CLASSES,
-                  n_streams=1, depth=12, source="frames", deadline_ms=20.0) -> dict:
+                  n_streams=1, depth=12, source="frames", deadline_ms=20.0,
+                  park_idle_ms=None) -> dict:
     """Both modes on the same trace; returns their summaries. source: "frames"
     (foveated beforehand) or "render" (foveated on the device per request);
-    deadline_ms: frames waiting longer on the host are shed (None: never)."""
+    deadline_ms: frames waiting longer on the host are shed (None: never);
+    park_idle_ms: park idle viewers to admit joining ones (None: never)."""
     dev = torch.device("cuda") if device is None else torch.device(device)
     specs = viewer_mix(n_viewers, duration_s, seed, rate_hz, classes)
     trace = arrivals(specs, seed)
@@ -496,7 +595,8 @@ def serve_compare(n_viewers=64, duration_s=10.0, budget_gb=60.0, seed=0, frames_
            "outputs": "every frame resolved into its viewer's output buffer (fused update + resolve)"}
     for mode in ("batched", "plain"):
         srv = Server(specs, pool, int(budget_gb * 1e9), mode=mode, n_streams=n_streams, depth=depth,
-                     device=dev, batch_launch=batch_launch, deadline_ms=deadline_ms)
+                     device=dev, batch_launch=batch_launch, deadline_ms=deadline_ms,
+                     park_idle_ms=park_idle_ms)
         out[mode] = srv.run(trace, duration_s).summary()
         srv.close()
         torch.cuda.synchronize(dev)

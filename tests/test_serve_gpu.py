@@ -1,6 +1,7 @@
 """Serving on the GPU: continuous batching and the plain path serve the same
 trace; every viewer's reservoirs are bit-identical to serving it alone; the
-HBM budget queues viewers that do not fit."""
+HBM budget queues viewers that do not fit, or parks idle ones in host memory
+(wrs_export_state / wrs_import_state) to admit them."""
 import numpy as np
 import pytest
 import torch
@@ -79,4 +80,51 @@ def test_budget_queues_viewers():
     assert stats.peak_state_bytes <= budget
     assert stats.viewers_queued_max > 0 and stats.frames_rejected > 0
     assert stats.frames_served + stats.frames_rejected == len(trace)
+    srv.close()
+
+
+def _phased_trace(vids_by_phase, phase_s, rate_hz):
+    # viewers take turns: in phase i only vids_by_phase[i % len] send frames
+    ev = []
+    n = int(round(phase_s * rate_hz))
+    for i, vids in enumerate(vids_by_phase):
+        for vid in vids:
+            for k in range(n):
+                ev.append((i * phase_s + (k + 0.5 + 0.1 * vid) / rate_hz, vid))
+    ev.sort()
+    return ev
+
+
+@pytest.mark.parametrize("mode", ["batched", "plain"])
+def test_budget_parks_idle_viewers_and_restores_them_bit_exact(mode):
+    # four viewers, room for two: viewers 0, 1 and 2, 3 take turns sending
+    # frames. A waiting viewer is admitted by parking idle ones in host memory;
+    # a parked viewer whose frame is due is restored by parking others. Every
+    # viewer's reservoirs and last resolved frame equal those of the viewer
+    # served alone with the same frames.
+    dev = torch.device("cuda")
+    w, h, radii = SMALL[1]
+    phases = [(0, 1), (2, 3), (0, 1), (2, 3)]
+    phase_s, duration = 0.25, 1.0
+    specs = [serve.ViewerSpec(vid=i, width=w, height=h, K=8 if i % 2 == 0 else 4, radii=radii, seed=i + 1,
+                              rate_hz=200.0, join_s=0.0, leave_s=duration, cls=0) for i in range(4)]
+    trace = _phased_trace(phases, phase_s, 200.0)
+    pool = serve.FramePool((SMALL[1],), 4, dev, seed=3)
+    budget = 2 * max(v.state_bytes() + v.frame_bytes() for v in specs)
+    srv = serve.Server(specs, pool, budget_bytes=budget, mode=mode, device=dev, keep_states=True,
+                       park_idle_ms=40.0)
+    stats = srv.run(trace, duration)
+    s = stats.summary()
+    assert stats.frames_served + stats.frames_rejected + stats.frames_shed == len(trace)
+    assert stats.peak_device_bytes <= budget
+    assert s["viewers_parked"] >= 2 and s["viewers_restored"] >= 1, s
+    assert set(srv.kept) == {0, 1, 2, 3}
+    for vid, st in srv.kept.items():
+        alone, out = serve.replay_alone(srv.specs[vid], srv.pushed[vid], pool, device=dev)
+        torch.cuda.synchronize()
+        assert st.frame_index == alone.frame_index == len(srv.pushed[vid])
+        assert np.array_equal(st.export_raw(), alone.export_raw()), f"viewer {vid}"
+        if srv.pushed[vid]:
+            assert torch.equal(srv.kept_out[vid].view(torch.int32), out.view(torch.int32)), f"viewer {vid}"
+        alone.close()
     srv.close()
