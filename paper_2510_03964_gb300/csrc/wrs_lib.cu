@@ -164,10 +164,12 @@ static int wrs_default_stages(int K, bool f16, int px) {
 }
 
 void wrs_default_pipe(int K, bool f16, int* px, int* stages) {
-  // 256-pixel tiles with the stages above: K = 8 FP32 gets two stages at two
-  // CTAs per SM, K = 8 FP16 three, K <= 4 four
-  *px = 1;
-  *stages = wrs_default_stages(K, f16, 1);
+  // 256-pixel tiles with the stages above (K = 8 FP32 gets two stages at two
+  // CTAs per SM, K = 8 FP16 three, K = 4 four); one or two slots take two
+  // pixels per thread (512-pixel tiles, four stages): their kernels are bound
+  // by instruction issue, and a thread's second pixel shares its per-tile work
+  *px = K <= 2 ? 2 : 1;
+  *stages = wrs_default_stages(K, f16, *px);
 }
 
 extern "C" size_t wrs_state_bytes(const wrs_config* cfg) {
@@ -497,7 +499,8 @@ extern "C" int wrs_push_foveated(wrs_ctx* x, const float* d_img, int64_t img_pit
   f.t = x->t;
   f.map_lo = wrs_map_lo(x);
   int px = x->pipe_px, stages = x->pipe_stages;
-  if (px != 1) wrs_default_pipe(x->cfg.K, x->cfg.color_fp16 != 0, &px, &stages);
+  // the foveating form takes one pixel per thread: its own stage count then
+  if (px != 1) stages = wrs_default_stages(x->cfg.K, x->cfg.color_fp16 != 0, 1);
   cudaError_t e = wrs_launch_pipe_fov(s, f, fv, filter, x->cfg.color_fp16 != 0, stages, x->sms,
                                       x->pipe_ctas, wrs_status_word(x), x->timeout_ns,
                                       static_cast<cudaStream_t>(stream));

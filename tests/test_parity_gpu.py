@@ -87,15 +87,17 @@ def test_pipeline_rejects_oversized_stages():
     st.close()
 
 
-@pytest.mark.parametrize("K,fp16,stages", [(8, False, 2), (8, True, 3), (4, False, 4), (4, True, 4),
-                                            (16, False, 2)])
-def test_default_stages_keep_two_ctas_per_sm(K, fp16, stages):
-    # as many stages (up to four) as keep two CTAs on an SM, else what one CTA holds
+@pytest.mark.parametrize("K,fp16,px,stages", [(8, False, 1, 2), (8, True, 1, 3), (4, False, 1, 4),
+                                               (4, True, 1, 4), (16, False, 1, 2), (1, False, 2, 4),
+                                               (2, True, 2, 4)])
+def test_default_stages_keep_two_ctas_per_sm(K, fp16, px, stages):
+    # as many stages (up to four) as keep two CTAs on an SM, else what one CTA
+    # holds; one or two slots take two pixels per thread
     import paper_2510_03964_gb300 as wrs
     st = wrs.Stream(64, 16, K, 8.0, color_fp16=fp16, device=torch.device("cuda"))
-    assert st.get_pipeline() == (True, 1, stages, 0)
+    assert st.get_pipeline() == (True, px, stages, 0)
     st.set_pipeline(True, 0, 0)
-    assert st.get_pipeline() == (True, 1, stages, 0)
+    assert st.get_pipeline() == (True, px, stages, 0)
     st.close()
 
 
