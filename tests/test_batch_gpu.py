@@ -14,6 +14,7 @@ pytestmark = pytest.mark.gpu
 MIX = [  # width, height, K, fp16, r_f
     (96, 40, 4, False, 10.0), (128, 32, 8, True, 12.0), (64, 16, 3, False, 6.0),
     (200, 8, 8, False, 20.0), (36, 20, 1, True, 5.0), (256, 12, 16, True, 30.0),
+    (48, 24, 2, False, 7.0),
 ]
 
 

@@ -70,6 +70,8 @@ class ReprojRun:
     {},
     {"color_fp16": True},
     {"K": 1, "update_rule": 1},
+    {"K": 1},
+    {"K": 2, "color_fp16": True},
     {"K": 3, "temporal_bias": 2},
     {"depth": False},
     {"motion": False},
