@@ -746,10 +746,15 @@ def roofline_line(spec, kernel_avg_ms, rho, peaks, workload_name, kname, window)
     bpp = (algorithmic_bytes_per_px(spec.K, spec.color_fp16, lit)
            + rho * replacement_bytes(spec.color_fp16, lit))
     achieved = bpp * hw / (kernel_avg_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(kname, workload_name, window)
+    src = ("measured (MEASURED_PEAKS.json hbm_gbs, copy)" if peaks["source"] == "measured"
+           else "fallback (no MEASURED_PEAKS.json: 6.8 TB/s, an earlier copy measurement on a GB300)")
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
             "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-            "traffic": recorded_traffic(kname, workload_name, window),
-            "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs, copy)",
+            "traffic": traffic,
+            "traffic_over_algorithmic": None if traffic is None else round(traffic / (bpp * hw), 4),
+            "traffic_window": window if traffic is not None else None,
+            "peak_source": src,
             "algorithmic_bytes_per_px": round(bpp, 2),
             "bytes_rule": f"{algorithmic_bytes_per_px(spec.K, spec.color_fp16, lit)} B read/written "
                           f"by every pixel-update + replacement rate {rho:.4f} (counted on the "
